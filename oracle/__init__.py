@@ -1,0 +1,239 @@
+"""FP64 CPU oracle for BTO Lagrangian flow-map extraction.
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The product path
+(the CUDA library and its binding) never does, and this package imports
+nothing from it.
+
+The arithmetic lives in ``bto_oracle.c`` (plain C, IEEE double, one particle
+at a time, OpenMP over particles). This module only marshals numpy arrays
+into it and strings the per-cycle calls into an interval, in the order the
+paper states (Sec. 2.3 and 3.1): seed on a uniform lattice, advance every live
+particle one RK4 step per cycle on that cycle's field, terminate on leaving
+the block, and write seed / end / valid at the end of the interval.
+
+Parity pins: every function here is pinned by tests that do not call the
+oracle's own formulas (closed forms for affine and rotating fields, brute
+force exit cycles, the Eq. (hx) invariant); see ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bto_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libbto_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``bto_oracle.c`` with gcc into ``oracle/_build``.
+
+    ``-ffp-contract=off`` keeps the double arithmetic free of fused
+    multiply-adds, so x86 and Arm hosts give identical results.
+    """
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    fp = ctypes.POINTER(ctypes.c_float)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.bto_oracle_num_seeds.argtypes = [i64p, ctypes.c_int64]
+    lib.bto_oracle_num_seeds.restype = ctypes.c_int64
+    lib.bto_oracle_seeds.argtypes = [i64p, dp, dp, ctypes.c_int64, ctypes.c_int64, i64p, dp]
+    lib.bto_oracle_seeds.restype = None
+    lib.bto_oracle_sample.argtypes = [fp, i64p, dp, dp, ctypes.c_int64, dp, dp]
+    lib.bto_oracle_sample.restype = None
+    lib.bto_oracle_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int32,
+                                     ctypes.c_int64, dp, i32p, dp, ctypes.c_int32]
+    lib.bto_oracle_cycle.restype = None
+    lib.bto_oracle_max_threads.argtypes = []
+    lib.bto_oracle_max_threads.restype = ctypes.c_int32
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+@dataclass(frozen=True)
+class Grid:
+    """One block of a uniform grid (reading R5): ``n`` cells per axis,
+    ``n + 1`` nodes per axis at ``origin + i * h``.
+
+    ``origin`` and ``h`` hold the float32 values the GPU receives, widened to
+    double, so both sides start from the same numbers.
+    """
+    n: tuple
+    origin: tuple
+    h: tuple
+
+    @staticmethod
+    def make(n, origin, h) -> "Grid":
+        o32 = np.asarray(origin, dtype=np.float32).astype(np.float64)
+        h32 = np.asarray(h, dtype=np.float32).astype(np.float64)
+        return Grid(tuple(int(v) for v in n), tuple(float(v) for v in o32),
+                    tuple(float(v) for v in h32))
+
+    def _arrays(self):
+        return (np.ascontiguousarray(self.n, dtype=np.int64),
+                np.ascontiguousarray(self.origin, dtype=np.float64),
+                np.ascontiguousarray(self.h, dtype=np.float64))
+
+    @property
+    def node_shape(self):
+        """numpy shape of a field for this block: (nz+1, ny+1, nx+1, 3)."""
+        return (self.n[2] + 1, self.n[1] + 1, self.n[0] + 1, 3)
+
+
+def max_threads() -> int:
+    return int(_load().bto_oracle_max_threads())
+
+
+def num_seeds(grid: Grid, stride: int) -> int:
+    n, _, _ = grid._arrays()
+    return int(_load().bto_oracle_num_seeds(_ptr(n, ctypes.c_int64), int(stride)))
+
+
+def seeds(grid: Grid, stride: int, ids=None) -> np.ndarray:
+    """Seed positions (physical), canonical order, shape (m, 3) float64."""
+    lib = _load()
+    n, o, h = grid._arrays()
+    if ids is None:
+        m = num_seeds(grid, stride)
+        idp = None
+    else:
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        m = ids.shape[0]
+        idp = _ptr(ids, ctypes.c_int64)
+    out = np.empty((m, 3), dtype=np.float64)
+    lib.bto_oracle_seeds(_ptr(n, ctypes.c_int64), _ptr(o, ctypes.c_double),
+                         _ptr(h, ctypes.c_double), int(stride), m, idp,
+                         _ptr(out, ctypes.c_double))
+    return out
+
+
+def _check_field(grid: Grid, field: np.ndarray) -> np.ndarray:
+    field = np.ascontiguousarray(field, dtype=np.float32)
+    want = int(np.prod(grid.node_shape))
+    if field.size != want:
+        raise ValueError(f"field has {field.size} values, block needs {want}")
+    return field
+
+
+def sample(grid: Grid, field: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Trilinear velocity at physical points q (m, 3) -> (m, 3) float64."""
+    lib = _load()
+    field = _check_field(grid, field)
+    n, o, h = grid._arrays()
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, 3)
+    v = np.empty_like(q)
+    lib.bto_oracle_sample(_ptr(field, ctypes.c_float), _ptr(n, ctypes.c_int64),
+                          _ptr(o, ctypes.c_double), _ptr(h, ctypes.c_double),
+                          q.shape[0], _ptr(q, ctypes.c_double), _ptr(v, ctypes.c_double))
+    return v
+
+
+class State:
+    """Particle state of one interval: positions, exit cycle, min margin."""
+
+    def __init__(self, x0: np.ndarray):
+        self.x = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, 3).copy()
+        self.seeds = self.x.copy()
+        m = self.x.shape[0]
+        self.exit_cycle = np.full(m, -1, dtype=np.int32)
+        self.min_margin = np.full(m, np.inf, dtype=np.float64)
+
+    @property
+    def valid(self) -> np.ndarray:
+        return (self.exit_cycle < 0).astype(np.uint8)
+
+
+def cycle(grid: Grid, field: np.ndarray, dt: float, c: int, state: State,
+          nthreads: int = 0) -> None:
+    """Advance every live particle of ``state`` by one RK4 step (in place)."""
+    lib = _load()
+    field = _check_field(grid, field)
+    n, o, h = grid._arrays()
+    lib.bto_oracle_cycle(_ptr(field, ctypes.c_float), _ptr(n, ctypes.c_int64),
+                         _ptr(o, ctypes.c_double), _ptr(h, ctypes.c_double),
+                         float(dt), int(c), state.x.shape[0],
+                         _ptr(state.x, ctypes.c_double),
+                         _ptr(state.exit_cycle, ctypes.c_int32),
+                         _ptr(state.min_margin, ctypes.c_double), int(nthreads))
+
+
+def run_interval(grid: Grid, stride: int, cycles: int, dt: float, field_of_cycle,
+                 ids=None, c0: int = 0, nthreads: int = 0) -> State:
+    """One interval (Sec. 2.3 / 3.1): seed, then ``cycles`` RK4 cycles.
+
+    ``field_of_cycle(c)`` returns the float32 field of cycle c (absolute cycle
+    index, starting at ``c0``); exit cycles are recorded relative to the
+    interval (0 .. cycles-1). ``ids`` restricts the run to those canonical
+    seeds (each particle is independent, so a subset gives the same numbers).
+    """
+    st = State(seeds(grid, stride, ids))
+    for c in range(cycles):
+        cycle(grid, field_of_cycle(c0 + c), dt, c, st, nthreads)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# Accuracy metrics (Sec. 4.3): b = BTO positions, m = reference positions.
+# ---------------------------------------------------------------------------
+def total_average_l2(b: np.ndarray, m: np.ndarray) -> float:
+    """Total average L2 norm, (1/p) sum_i ||b_i - m_i|| (Sec. 4.3). The sum
+    runs over the p particles (the printed bounds i = 0..p are read as the p
+    particles, matching the 1/p factor)."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 3)
+    m = np.asarray(m, dtype=np.float64).reshape(-1, 3)
+    if b.shape[0] == 0:
+        return 0.0
+    return float(np.mean(np.sqrt(np.sum((b - m) ** 2, axis=1))))
+
+
+def accuracy_percent(l2: float, cell_side: float) -> float:
+    """Accuracy% = (C - L) / C * 100 (Sec. 4.3)."""
+    return (cell_side - l2) / cell_side * 100.0
+
+
+def max_l2(b: np.ndarray, m: np.ndarray) -> float:
+    """Largest single-particle L2 error of one interval (Sec. 4.3)."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 3)
+    m = np.asarray(m, dtype=np.float64).reshape(-1, 3)
+    if b.shape[0] == 0:
+        return 0.0
+    return float(np.max(np.sqrt(np.sum((b - m) ** 2, axis=1))))
+
+
+def greatest_and_average_max_l2(per_interval_max) -> tuple:
+    """Greatest max L2 over intervals, and the mean of the per-interval
+    maxima (Sec. 4.3)."""
+    a = np.asarray(per_interval_max, dtype=np.float64)
+    return float(a.max()), float(a.mean())
