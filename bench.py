@@ -1,0 +1,617 @@
+#!/usr/bin/env python3
+"""Benchmark: RK4 particle-steps/s of BTO flow-map extraction on GB300.
+
+Workload (default, ``turb256``): a 256^3-cell domain split into 2x2x2 blocks of
+128^3 cells (129^3 shared-face nodes each), FP32 float3 divergence-free
+Fourier-mode turbulence (64 modes, |k| in [1,16], amplitude |k|^-5/6, phases
+drifting per cycle, seed 20040204), one seed per 2^3 cells (262,144 per block,
+2,097,152 in all), an interval of 100 cycles, dt = 0.25 cell / max|u|.
+
+One bench STEP is one interval of the whole hot path over that input: 100
+advection cycles of all 8 blocks (one persistent launch per cycle) and the
+interval end (basis-flow writer and reseed). The 100 per-cycle fields
+(8 x 100 x 25.7 MB = 20.6 GB, F3 layout) are synthesised in HBM before the
+timed region, so every cycle reads a field larger than L2 that was not
+recently touched.
+
+Printed JSON (one line, rank 0): value = particle-steps per second over the
+whole step, roofline of the advection kernel against the measured HBM copy
+peak, the FP64 CPU oracle's rate on a bounded sample, and an end-to-end
+figure with the fields copied from pinned host memory every cycle.
+
+Also reported: the same workload as 8 separate single-block contexts
+(``plain``), as one CUDA graph per interval (``graph``), the paper's metric
+that excludes the write cycle, and the accuracy cost of BTO against the
+in-GPU global flow map in which particles cross blocks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEED = 20040204
+GLOBAL_CELLS = 256
+BLOCK_CELLS = 128
+STRIDE = 2
+INTERVAL = 100
+NMODES = 64
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/graph/global-map/e2e legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_init(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def block_layout():
+    nbx = GLOBAL_CELLS // BLOCK_CELLS
+    h = 1.0 / GLOBAL_CELLS
+    blocks = []
+    for bz in range(nbx):
+        for by in range(nbx):
+            for bx in range(nbx):
+                blocks.append((bx, by, bz))
+    ext = [(BLOCK_CELLS,) * 3] * len(blocks)
+    org = [(b[0] * BLOCK_CELLS * h, b[1] * BLOCK_CELLS * h, b[2] * BLOCK_CELLS * h) for b in blocks]
+    spc = [(h, h, h)] * len(blocks)
+    return blocks, ext, org, spc
+
+
+def synth_fields(modes, blocks, cycles, device, with_global=False):
+    """Per-cycle block fields (F3, contiguous) generated in device memory."""
+    import torch
+    from paper_2004_02003_gb300 import inputs
+    G = GLOBAL_CELLS
+    h = 1.0 / G
+    n = BLOCK_CELLS
+    per_cycle, glob = [], []
+    for c in range(cycles):
+        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), c, device)
+        row = []
+        for (bx, by, bz) in blocks:
+            row.append(gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous())
+        per_cycle.append(row)
+        if with_global:
+            glob.append(gf)
+        else:
+            del gf
+    torch.cuda.synchronize()
+    return per_cycle, glob
+
+
+def count_particle_steps(exit_cycle, L):
+    """Particle-steps of an interval: each particle attempts one step per cycle
+    while live at the cycle's start, i.e. L steps if valid, exit+1 otherwise."""
+    e = exit_cycle.astype(np.int64)
+    return int(np.where(e < 0, L, e + 1).sum())
+
+
+def live_per_cycle(exit_cycle, L):
+    e = exit_cycle.astype(np.int64)
+    steps = np.where(e < 0, L, e + 1)
+    return np.array([(steps > c).sum() for c in range(L)], dtype=np.int64)
+
+
+def touched_nodes(ctx, act, n_cells, nb):
+    """Nodes of the cells that hold a live particle at the start of the current
+    cycle, summed over blocks: the nodes the cycle's first RK4 stage must read
+    (a lower bound of all nodes the cycle touches: later stage points may
+    reach a neighbour cell)."""
+    import torch
+    live = ctx.copy_active(act)
+    off = ctx.offsets()
+    n = n_cells
+    total = 0
+    for b in range(nb):
+        x = act[off[b]:off[b] + live[b], :3]
+        if x.shape[0] == 0:
+            continue
+        cell = torch.clamp(torch.floor(x).to(torch.int64), 0, n - 1)
+        mark = torch.zeros((n + 1) ** 3, dtype=torch.bool, device=act.device)
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    idx = (cell[:, 0] + dx) + (n + 1) * ((cell[:, 1] + dy) + (n + 1) * (cell[:, 2] + dz))
+                    mark[idx] = True
+        total += int(mark.sum().item())
+    return total
+
+
+def algorithmic_bytes(live, nodes_touched, L):
+    """SURVEY-defined algorithmic bytes of cycle c:
+    12 * nodes touched + 24 * live at start + 17 * terminated in the cycle."""
+    term = np.zeros(L, dtype=np.int64)
+    term[:-1] = live[:-1] - live[1:]
+    return 12 * nodes_touched + 24 * live + 17 * term
+
+
+def run_ours(args):
+    import torch
+    from paper_2004_02003_gb300 import bto, inputs
+    from paper_2004_02003_gb300 import build as lib_build
+
+    rank, world, local = dist_init(args.gpus)
+    lib_build.build()
+    bto.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    modes = inputs.fourier_modes(SEED, m=NMODES, kmin=1.0, kmax=16.0, drift_max=0.05)
+    h = 1.0 / GLOBAL_CELLS
+    dt = 0.25 * h  # max|u| = 1 after normalisation -> 0.25 cells per step at max speed
+    blocks, ext, org, spc = block_layout()
+    nb = len(blocks)
+    L = INTERVAL
+    fields, gfields = synth_fields(modes, blocks, L, dev, with_global=(rank == 0 and not args.no_extras))
+    table = torch.tensor([f.data_ptr() for row in fields for f in row], dtype=torch.int64, device=dev)
+    field_bytes_cycle = sum(f.numel() * 4 for f in fields[0])
+
+    ctx = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+    P = ctx.P
+    out = ctx.alloc_outputs(dev)
+
+    def one_step(launch_events=None):
+        for c in range(L):
+            if launch_events is not None:
+                launch_events[c][0].record(stream)
+            ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+            if launch_events is not None:
+                launch_events[c][1].record(stream)
+        ctx.end_interval(out)
+
+    # untimed reference interval: exit cycles define the units of every step,
+    # and the live particles' cells give the field nodes each cycle touches
+    act = torch.empty((P, 4), dtype=torch.float32, device=dev)
+    nodes_touched = np.zeros(L, dtype=np.int64)
+    for c in range(L):
+        nodes_touched[c] = touched_nodes(ctx, act, BLOCK_CELLS, nb)
+        ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    ctx.end_interval(out)
+    torch.cuda.synchronize()
+    ctx.check()
+    exit_np = out["exit_cycle"].cpu().numpy()
+    valid_np = out["valid"].cpu().numpy()
+    psteps = count_particle_steps(exit_np, L)
+    live = live_per_cycle(exit_np, L)
+    nodes_total = nb * (BLOCK_CELLS + 1) ** 3
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(L)]
+    launch_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            one_step(ev)
+            if k == args.steps - 1:
+                pass
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    elapsed = t0.elapsed_time(t1) / 1e3
+    # per-launch durations of the last step (same work every step)
+    launch_ms = [ev[c][0].elapsed_time(ev[c][1]) for c in range(L)]
+    ctx.check()
+    # every step computes the same interval: check it reproduced the units
+    assert np.array_equal(out["exit_cycle"].cpu().numpy(), exit_np), "steps differ"
+
+    elapsed_max = max_over_ranks(elapsed, world)
+    total_psteps = sum_over_ranks(float(psteps * args.steps), world)
+    value = total_psteps / elapsed_max
+    advect_s = sum(launch_ms) / 1e3
+
+    # roofline of the advection kernel (dominant): algorithmic bytes of each
+    # launch (12 B per touched node, 24 B per live particle, 17 B per
+    # termination) over the measured launch durations
+    import json as _json
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    algo = algorithmic_bytes(live, nodes_touched, L)
+    achieved = float(algo.sum()) / advect_s / 1e9
+    frac = achieved / peak
+
+    res = {
+        "metric": "RK4 particle-steps/s on 1 GB300 (% of mem roofline); batched & adjoint vs plain",
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_max / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": "turb256: 256^3 cells as 2x2x2 blocks of 128^3, Fourier turbulence (64 modes), "
+                        "stride 2 (2,097,152 particles), interval 100, dt=0.25 cell/max|u|",
+            "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
+            "field_layout": "F3_AOS", "field_bytes_per_cycle": field_bytes_cycle,
+            "l2": "inputs larger than L2: each cycle reads its own 206 MB field, 100 distinct fields per step",
+            "launch": ctx.launch(),
+            "parallelism": f"weak: {world} rank(s), each the full workload, no collective",
+        },
+        "units_per_step": psteps,
+        "nodes_touched_frac": float(nodes_touched.mean() / nodes_total),
+        "paper_metric_value": float(psteps) / advect_s if advect_s > 0 else None,
+        "terminated_frac": float(1.0 - valid_np.mean()),
+        "gpu_launches": args.steps * (L + 3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": frac,
+                     "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": float(algo.mean()),
+                     "avg_launch_ms": float(np.mean(launch_ms))},
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras:
+        res.update(extras(args, ctx, fields, gfields, table, out, exit_np, psteps, dt, dev, stream, rank, world,
+                          ext, org, spc))
+    if rank == 0 and world == 1:
+        res["cpu_baseline"] = cpu_baseline(fields, dt, args.cpu_seconds)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, stream, rank, world, ext, org, spc):
+    import torch
+    from paper_2004_02003_gb300 import bto
+    L = INTERVAL
+    nb = len(ext)
+    res = {}
+    # (1) plain: one single-block context per block, one launch per block and cycle
+    plain = [bto.Context(ext[b], org[b], spc[b], STRIDE, L) for b in range(nb)]
+    outs = [p.alloc_outputs(dev) for p in plain]
+
+    def plain_step():
+        for c in range(L):
+            for b in range(nb):
+                plain[b].advect(fields[c][b], dt)
+        for b in range(nb):
+            plain[b].end_interval(outs[b])
+
+    for _ in range(max(1, args.warmup)):
+        plain_step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        plain_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    res["plain_value"] = psteps * args.steps / (t0.elapsed_time(t1) / 1e3)
+    for p in plain:
+        p.check(); p.close()
+
+    # (2) graph: the interval's cycles as one CUDA graph
+    g = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+    gout = g.alloc_outputs(dev)
+    for _ in range(max(1, args.warmup)):
+        g.interval_graph(table, dt)
+        g.end_interval(gout)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        g.interval_graph(table, dt)
+        g.end_interval(gout)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    assert np.array_equal(gout["exit_cycle"].cpu().numpy(), exit_ref)
+    res["graph_value"] = psteps * args.steps / (t0.elapsed_time(t1) / 1e3)
+    g.close()
+
+    # (3) accuracy cost vs the global flow map (rank 0, untimed)
+    if rank == 0 and gfields:
+        G = GLOBAL_CELLS
+        h = 1.0 / G
+        gc = bto.Context((G, G, G), (0, 0, 0), (h, h, h), STRIDE, L)
+        for c in range(L):
+            gc.advect(gfields[c], dt)
+        go = gc.end_interval()
+        gc.check()
+        torch.cuda.synchronize()
+        gv = go["valid"].cpu().numpy()
+        ge = go["ends"].cpu().numpy().astype(np.float64)
+        gce = go["exit_cycle"].cpu().numpy()
+        gc.close()
+        # global id of each block seed
+        n = BLOCK_CELLS // STRIDE
+        GS = G // STRIDE
+        nbx = G // BLOCK_CELLS
+        gid = []
+        for bz in range(nbx):
+            for by in range(nbx):
+                for bx in range(nbx):
+                    j = np.arange(n ** 3)
+                    jx, jy, jz = j % n + bx * n, (j // n) % n + by * n, j // (n * n) + bz * n
+                    gid.append(jx + GS * (jy + GS * jz))
+        gid = np.concatenate(gid)
+        bv = out["valid"].cpu().numpy()
+        be = out["ends"].cpu().numpy().astype(np.float64)
+        ok = bv == 1
+        dev_cells = float(np.max(np.abs(be[ok] - ge[gid][ok])) / h) if ok.any() else 0.0
+        res["accuracy_vs_global"] = {
+            "terminated_frac_bto": float(1 - bv.mean()),
+            "terminated_frac_global": float(1 - gv.mean()),
+            "bto_valid_but_global_invalid": int((ok & (gv[gid] == 0)).sum()),
+            "max_valid_end_deviation_cells": dev_cells,
+            "global_particle_steps": count_particle_steps(gce, L),
+        }
+
+    # (4) end to end: fields copied from pinned host memory every cycle,
+    # basis flows copied back every interval; copies overlap compute on a
+    # second stream with a two-slot device ring.
+    res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb)
+    return res
+
+
+def e2e(args, ctx, fields, dt, dev, stream, nb):
+    import torch
+    L = INTERVAL
+    R = 8  # pinned host ring of per-cycle fields (cycle c uses host[c % R])
+    host = [[torch.empty(f.shape, dtype=torch.float32, pin_memory=True) for f in fields[0]] for _ in range(R)]
+    for r in range(R):
+        for b in range(nb):
+            host[r][b].copy_(fields[r][b])
+    slots = [[torch.empty_like(f) for f in fields[0]] for _ in range(2)]
+    slot_ptrs = [torch.tensor([t.data_ptr() for t in s], dtype=torch.int64, device=dev) for s in slots]
+    out_host = {"seeds": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
+                "ends": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
+                "valid": torch.empty((ctx.P,), dtype=torch.uint8, pin_memory=True),
+                "exit_cycle": torch.empty((ctx.P,), dtype=torch.int32, pin_memory=True)}
+    copy_stream = torch.cuda.Stream(device=dev)
+    out_dev = ctx.alloc_outputs(dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    h2d_bytes = sum(t.numel() * 4 for t in host[0])
+    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host.values())
+
+    def step():
+        for c in range(L):
+            s = c & 1
+            with torch.cuda.stream(copy_stream):
+                if c >= 2:
+                    copy_stream.wait_event(consumed[s])
+                for b in range(nb):
+                    slots[s][b].copy_(host[c % R][b], non_blocking=True)
+                copied[s].record(copy_stream)
+            stream.wait_event(copied[s])
+            ctx.advect_batch(slot_ptrs[s], dt)
+            consumed[s].record(stream)
+        ctx.end_interval(out_dev)
+        for k in out_host:
+            out_host[k].copy_(out_dev[k], non_blocking=True)
+        stream.synchronize()
+        return count_particle_steps(out_host["exit_cycle"].numpy(), L)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    t = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        units += step()
+    el = time.perf_counter() - t
+    return {"value": units / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
+            "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def cpu_baseline(fields, dt, seconds, block=0):
+    import oracle
+    h = 1.0 / GLOBAL_CELLS
+    g = oracle.Grid.make((BLOCK_CELLS,) * 3, (0, 0, 0), (h, h, h))
+    return _time_oracle(g, fields, dt, seconds, block, oracle.max_threads())
+
+
+def _time_oracle(g, fields, dt, seconds, block, nthreads):
+    import oracle
+    st = oracle.State(oracle.seeds(g, STRIDE))
+    steps, spent, c = 0, 0.0, 0
+    while c < INTERVAL and spent < seconds:
+        f = fields[c][block]
+        f = f.cpu().numpy() if hasattr(f, "cpu") else f
+        live = int((st.exit_cycle < 0).sum())
+        t = time.perf_counter()
+        oracle.cycle(g, f, dt, c, st)
+        spent += time.perf_counter() - t
+        steps += live
+        c += 1
+    return {"value": steps / spent, "unit": "particle-steps/s", "cores": nthreads,
+            "host_cpus": os.cpu_count(), "kind": "oracle",
+            "sample": f"block 0 of 8 (262,144 particles), cycles 0..{c - 1} of 100 "
+                      f"({steps} particle-steps, {spent:.1f} s)"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm (rank 0 only, bounded sample)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    from paper_2004_02003_gb300 import inputs
+    import oracle
+    oracle.build()
+    modes = inputs.fourier_modes(SEED, m=NMODES, kmin=1.0, kmax=16.0, drift_max=0.05)
+    h = 1.0 / GLOBAL_CELLS
+    dt = 0.25 * h
+    g = oracle.Grid.make((BLOCK_CELLS,) * 3, (0, 0, 0), (h, h, h))
+    # a bounded sample per step: 8192 particles of block 0 over the full interval
+    rng = np.random.default_rng(SEED)
+    ids = np.sort(rng.choice(oracle.num_seeds(g, STRIDE), size=8192, replace=False))
+    fields = [inputs.fourier_field(modes, (BLOCK_CELLS,) * 3, (0, 0, 0), (h, h, h), c) for c in range(INTERVAL)]
+
+    def step():
+        st = oracle.State(oracle.seeds(g, STRIDE, ids))
+        n = 0
+        for c in range(INTERVAL):
+            n += int((st.exit_cycle < 0).sum())
+            oracle.cycle(g, fields[c], dt, c, st)
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        units += step()
+    el = time.perf_counter() - t
+    v = units / el
+    print(json.dumps({
+        "impl": "reference", "metric": "RK4 particle-steps/s on 1 GB300 (% of mem roofline); batched & adjoint vs plain",
+        "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "turb256 (bounded sample: 8192 random particles of block 0, full 100-cycle interval)"},
+        "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "8192 random particles of block 0 of 8, all 100 cycles, per step"},
+        "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

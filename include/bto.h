@@ -1,0 +1,198 @@
+/*
+ * bto.h -- C ABI of libbto: GB300 (sm_103a) Boundary Termination Optimization
+ * (BTO) Lagrangian flow-map extraction.
+ *
+ * The method (Sane et al., "Scalable In Situ Lagrangian Flow Map Extraction:
+ * Demonstrating the Viability of a Communication-Free Model"):
+ *   - Sec. 2.3: particles are seeded along a uniform grid at the start of an
+ *     interval; an interval is a fixed number of cycles after which the end
+ *     positions are saved and the particles reset onto the grid; a 1:X data
+ *     reduction places one particle per X grid points.
+ *   - Sec. 3.1: each cycle advances every particle by one RK4 step through
+ *     the velocity field of that cycle; a particle that would need another
+ *     block's data is terminated and its trajectory discarded; particle
+ *     management keeps terminated particles off the GPU threads.
+ *   - Sec. 3.3, Eq. (1): the velocity between nodes is the linear
+ *     interpolant per axis and per component (trilinear in 3D).
+ *
+ * Conventions of this library (the paper is silent on them):
+ *   - A block has n[a] CELLS per axis and (n[a]+1) velocity NODES per axis at
+ *     origin[a] + i*spacing[a], i = 0..n[a]. Neighbouring blocks share their
+ *     face node layer.
+ *   - The block is the CLOSED box [origin, origin + n*spacing]. Each RK4 stage
+ *     point (p2, p3, p4) and the end point are tested in that order; the first
+ *     one outside terminates the particle, which keeps its position from
+ *     before that step and records the cycle index.
+ *   - Seeds sit at node indices j*s (j = 0..ceil(n/s)-1 per axis); the seed
+ *     with lattice index (jx, jy, jz) has canonical id
+ *     p = jx + Sx*(jy + Sy*jz), S = ceil(n/s). Outputs are in canonical order.
+ *   - Cycles are numbered 0..interval_cycles-1 within each interval.
+ *
+ * Memory and streams: all pointers named d_* are DEVICE pointers of the
+ * current CUDA device; all others are host pointers. Every call that takes a
+ * stream enqueues its work on that stream and returns without waiting for it
+ * (no host synchronisation on the per-cycle path). The caller keeps d_field
+ * and output buffers valid until that stream work has completed. The library
+ * owns the context and all particle state; it never retains caller pointers
+ * beyond the stream work of the call that received them (except the field
+ * table given to bto_launch_interval_graph, see there).
+ *
+ * Errors: argument checks are synchronous and return BTO_ERR_INVALID_ARG
+ * without launching anything; calls out of order return BTO_ERR_STATE without
+ * launching anything; a failed launch returns BTO_ERR_CUDA. Device-side
+ * errors are sticky and reported by bto_last_error().
+ */
+#ifndef BTO_H
+#define BTO_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BTO_API __attribute__((visibility("default")))
+#else
+#define BTO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *bto_stream;
+
+typedef struct bto_ctx bto_ctx;
+
+typedef enum {
+    BTO_OK = 0,
+    BTO_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or value */
+    BTO_ERR_STATE = 2,       /* call out of order (see bto_advect_cycle) */
+    BTO_ERR_CUDA = 3,        /* a CUDA call or launch failed */
+    BTO_ERR_OOM = 4,         /* device or host allocation failed */
+    BTO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    BTO_ERR_UNSUPPORTED = 6  /* valid request this build does not handle */
+} bto_status;
+
+/* Field layouts accepted by bto_advect_cycle.
+ * F3_AOS: float32 x,y,z per node, 12 bytes per node, x index fastest
+ *         (node (i,j,k) at element i + (n0+1)*(j + (n1+1)*k)).
+ * F4_AOS: float32 x,y,z,pad per node, 16 bytes per node, same order;
+ *         the pad value is ignored; d_field must be 16-byte aligned. */
+typedef enum { BTO_FIELD_F3_AOS = 0, BTO_FIELD_F4_AOS = 1 } bto_field_layout;
+
+/* Create a context for one block (Sec. 2.3 problem statement: a block of a
+ * uniform grid, a seeding density and an interval length).
+ *   extent_cells[3]  cells per axis, each >= 1; nodes per block <= 2^29
+ *   origin[3]        physical position of node (0,0,0), finite
+ *   spacing[3]       physical cell size per axis, finite and > 0
+ *   seed_stride      s >= 1: one seed per s^3 grid points (1:s^3 reduction)
+ *   interval_cycles  L >= 1 cycles per interval
+ *   out              receives the context; unchanged on error
+ * Allocates the particle state on the current device and seeds the first
+ * interval (synchronously). Returns BTO_ERR_OOM if the device memory is not
+ * available. */
+BTO_API bto_status bto_create(const int32_t extent_cells[3], const float origin[3],
+                      const float spacing[3], int32_t seed_stride,
+                      int32_t interval_cycles, bto_ctx **out);
+
+/* Create one context for nb independent blocks of possibly different shapes
+ * that advance together, one persistent launch per cycle (the paper's
+ * per-rank blocks, Sec. 3.1, emulated on one device). Arrays have nb entries
+ * (extents, origins and spacings: nb*3 values, block-major). Seeds of block b
+ * occupy canonical ids offsets[b] .. offsets[b+1]-1 (bto_batch_offsets). */
+BTO_API bto_status bto_batch_create(int32_t nb, const int32_t *extents,
+                            const float *origins, const float *spacings,
+                            const int32_t *strides, int32_t interval_cycles,
+                            bto_ctx **out);
+
+/* Select the layout of the fields passed to the advect calls (default
+ * BTO_FIELD_F3_AOS). Only between intervals (cycle 0), else BTO_ERR_STATE. */
+BTO_API bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout);
+
+/* Total number of seeds P of the context (all blocks), or -1 for NULL. */
+BTO_API int64_t bto_num_seeds(const bto_ctx *ctx);
+
+/* Number of blocks of the context, or -1 for NULL. */
+BTO_API int32_t bto_num_blocks(const bto_ctx *ctx);
+
+/* offsets[nb+1] (host): first canonical id of each block, offsets[nb] = P. */
+BTO_API bto_status bto_batch_offsets(const bto_ctx *ctx, int64_t *offsets);
+
+/* One cycle of a single-block context (Sec. 3.1): every live particle takes
+ * one RK4 step through d_field with step dt (any finite value; negative
+ * integrates backward, 0 is a no-op step). Particles whose stage or end point
+ * leaves the block are terminated and removed from the active set.
+ *   d_field  device pointer to the block's nodes in the selected layout
+ * BTO_ERR_STATE if interval_cycles cycles were already advanced since the
+ * last bto_end_interval, or if ctx holds more than one block. */
+BTO_API bto_status bto_advect_cycle(bto_ctx *ctx, const void *d_field, float dt,
+                            bto_stream stream);
+
+/* One cycle of a batched context.
+ *   d_fields  DEVICE array of nb device pointers, entry b = field of block b
+ * The pointer array is read by the kernel on the stream. */
+BTO_API bto_status bto_batch_advect_cycle(bto_ctx *ctx, const void *const *d_fields,
+                                  float dt, bto_stream stream);
+
+/* End the interval (Sec. 2.3): write the basis flows in canonical order and
+ * reseed every block on its lattice.
+ *   d_seeds       P*3 floats: seed position (physical)
+ *   d_ends        P*3 floats: end position (physical); for a terminated
+ *                 particle, its last position inside the block
+ *   d_valid       P bytes: 1 = stayed in its block for the whole interval
+ *   d_exit_cycle  P int32 or NULL: cycle of termination, -1 if valid
+ * Every entry of every non-NULL buffer is written exactly once.
+ * BTO_ERR_STATE unless exactly interval_cycles cycles were advanced. */
+BTO_API bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends,
+                            uint8_t *d_valid, int32_t *d_exit_cycle,
+                            bto_stream stream);
+
+/* Capture the cycles of one interval of a context into a CUDA graph and
+ * launch it on `stream`; later intervals relaunch the cached graph.
+ *   d_field_table  DEVICE array of interval_cycles*nb device pointers,
+ *                  entry c*nb + b = field of block b in cycle c; it must
+ *                  stay valid (and its entries point at the fields) for as
+ *                  long as the graph is relaunched
+ *   dt             step of every cycle
+ * Equivalent to interval_cycles advect calls, but one graph launch.
+ * Must be called at cycle 0; leaves the context at cycle interval_cycles. */
+BTO_API bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_table,
+                                     float dt, bto_stream stream);
+
+/* Launch shape of the advection kernel: threads per CTA (128 or 256),
+ * particles per thread (1, 2 or 4) and CTAs per SM (0 = as many as fit).
+ * Results do not depend on it. Between intervals only. */
+BTO_API bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta,
+                          int32_t particles_per_thread, int32_t ctas_per_sm);
+
+/* Report the launch shape in use (host ints: threads, ppt, ctas_per_sm,
+ * grid size). */
+BTO_API bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[4]);
+
+/* Diagnostics (not for the per-cycle path): copy the active particle list as
+ * it stands before the next cycle.
+ *   d_out  P*4 floats (device); for block b, rows offsets[b] ..
+ *          offsets[b] + live[b] - 1 hold (xi_x, xi_y, xi_z, id bits) of its live
+ *          particles, xi = (x - origin) / spacing in block-local cell units and
+ *          id = canonical id within the block (int32 bits); other rows are
+ *          unspecified
+ *   live   nb int32 (host): live particles per block
+ * Waits for `stream`. */
+BTO_API bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live,
+                                   bto_stream stream);
+
+/* Sticky error of earlier asynchronous work of this context (a launch
+ * failure or a device-side error word); waits for the context's last stream
+ * work; clears the sticky state. */
+BTO_API bto_status bto_last_error(bto_ctx *ctx);
+
+/* Static string for a status code. */
+BTO_API const char *bto_status_string(bto_status status);
+
+/* Wait for outstanding work of the context, then free it. NULL is a no-op. */
+BTO_API void bto_destroy(bto_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTO_H */

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libbto (include/bto.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the CUDA library; nothing is
+computed here. Device buffers may be given as torch CUDA tensors (their
+``data_ptr()`` is passed) or as integer device addresses. Streams default to
+torch's current stream on the current device.
+
+The library must have been built (``paper_2004_02003_gb300.build.build()`` or
+``__graft_entry__.build()``); importing works without it, but the first call
+raises :class:`BtoError` if ``libbto.so`` is missing. There is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbto.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bto.h")
+
+BTO_OK = 0
+BTO_ERR_INVALID_ARG = 1
+BTO_ERR_STATE = 2
+BTO_ERR_CUDA = 3
+BTO_ERR_OOM = 4
+BTO_ERR_TIMEOUT = 5
+BTO_ERR_UNSUPPORTED = 6
+BTO_FIELD_F3_AOS = 0
+BTO_FIELD_F4_AOS = 1
+
+_lib = None
+
+
+class BtoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status) if _lib else status} (status {status})")
+
+
+def _declare(lib):
+    c_i32p = ctypes.POINTER(ctypes.c_int32)
+    c_i64p = ctypes.POINTER(ctypes.c_int64)
+    c_fp = ctypes.POINTER(ctypes.c_float)
+    vp = ctypes.c_void_p
+    sig = {
+        "bto_create": ([c_i32p, c_fp, c_fp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)], ctypes.c_int),
+        "bto_batch_create": ([ctypes.c_int32, c_i32p, c_fp, c_fp, c_i32p, ctypes.c_int32,
+                              ctypes.POINTER(vp)], ctypes.c_int),
+        "bto_set_field_layout": ([vp, ctypes.c_int], ctypes.c_int),
+        "bto_num_seeds": ([vp], ctypes.c_int64),
+        "bto_num_blocks": ([vp], ctypes.c_int32),
+        "bto_batch_offsets": ([vp, c_i64p], ctypes.c_int),
+        "bto_advect_cycle": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "bto_batch_advect_cycle": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "bto_end_interval": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "bto_launch_interval_graph": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
+        "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
+        "bto_last_error": ([vp], ctypes.c_int),
+        "bto_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "bto_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def load():
+    """Load libbto.so (raises BtoError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise BtoError(BTO_ERR_UNSUPPORTED, f"libbto not built ({LIB_PATH} missing)")
+        lib = ctypes.CDLL(LIB_PATH)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/bto.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bto_[a-z_0-9]+)\s*\(", text)))
+
+
+def status_string(status: int) -> str:
+    return load().bto_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != BTO_OK:
+        raise BtoError(status, where)
+
+
+def _addr(buf) -> int:
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    return int(buf.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _arr(ctype, values):
+    values = list(values)
+    return (ctype * len(values))(*values)
+
+
+def bto_create(extent_cells, origin, spacing, seed_stride: int, interval_cycles: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().bto_create(_arr(ctypes.c_int32, extent_cells), _arr(ctypes.c_float, origin),
+                             _arr(ctypes.c_float, spacing), int(seed_stride), int(interval_cycles),
+                             ctypes.byref(out)), "bto_create")
+    return out.value
+
+
+def bto_batch_create(extents, origins, spacings, strides, interval_cycles: int) -> int:
+    ext = [int(v) for e in extents for v in e]
+    org = [float(v) for o in origins for v in o]
+    spc = [float(v) for s in spacings for v in s]
+    nb = len(strides)
+    if len(ext) != 3 * nb or len(org) != 3 * nb or len(spc) != 3 * nb:
+        raise BtoError(BTO_ERR_INVALID_ARG, "bto_batch_create: array lengths")
+    out = ctypes.c_void_p()
+    _check(load().bto_batch_create(nb, _arr(ctypes.c_int32, ext), _arr(ctypes.c_float, org),
+                                   _arr(ctypes.c_float, spc), _arr(ctypes.c_int32, strides),
+                                   int(interval_cycles), ctypes.byref(out)), "bto_batch_create")
+    return out.value
+
+
+def bto_set_field_layout(ctx: int, layout: int) -> None:
+    _check(load().bto_set_field_layout(ctx, int(layout)), "bto_set_field_layout")
+
+
+def bto_num_seeds(ctx: int) -> int:
+    return int(load().bto_num_seeds(ctx))
+
+
+def bto_num_blocks(ctx: int) -> int:
+    return int(load().bto_num_blocks(ctx))
+
+
+def bto_batch_offsets(ctx: int) -> list:
+    nb = bto_num_blocks(ctx)
+    buf = (ctypes.c_int64 * (nb + 1))()
+    _check(load().bto_batch_offsets(ctx, buf), "bto_batch_offsets")
+    return list(buf)
+
+
+def bto_advect_cycle(ctx: int, d_field, dt: float, stream=None) -> None:
+    _check(load().bto_advect_cycle(ctx, _addr(d_field), float(dt), _stream(stream)), "bto_advect_cycle")
+
+
+def bto_batch_advect_cycle(ctx: int, d_fields, dt: float, stream=None) -> None:
+    _check(load().bto_batch_advect_cycle(ctx, _addr(d_fields), float(dt), _stream(stream)),
+           "bto_batch_advect_cycle")
+
+
+def bto_end_interval(ctx: int, d_seeds, d_ends, d_valid, d_exit_cycle=None, stream=None) -> None:
+    _check(load().bto_end_interval(ctx, _addr(d_seeds), _addr(d_ends), _addr(d_valid),
+                                   _addr(d_exit_cycle), _stream(stream)), "bto_end_interval")
+
+
+def bto_launch_interval_graph(ctx: int, d_field_table, dt: float, stream=None) -> None:
+    _check(load().bto_launch_interval_graph(ctx, _addr(d_field_table), float(dt), _stream(stream)),
+           "bto_launch_interval_graph")
+
+
+def bto_set_launch(ctx: int, threads_per_cta: int, particles_per_thread: int, ctas_per_sm: int = 0) -> None:
+    _check(load().bto_set_launch(ctx, int(threads_per_cta), int(particles_per_thread), int(ctas_per_sm)),
+           "bto_set_launch")
+
+
+def bto_get_launch(ctx: int) -> dict:
+    buf = (ctypes.c_int32 * 4)()
+    _check(load().bto_get_launch(ctx, buf), "bto_get_launch")
+    return {"threads_per_cta": buf[0], "particles_per_thread": buf[1], "ctas_per_sm": buf[2],
+            "grid": buf[3]}
+
+
+def bto_copy_active(ctx: int, d_out, stream=None) -> list:
+    nb = bto_num_blocks(ctx)
+    live = (ctypes.c_int32 * nb)()
+    _check(load().bto_copy_active(ctx, _addr(d_out), live, _stream(stream)), "bto_copy_active")
+    return list(live)
+
+
+def bto_last_error(ctx: int) -> int:
+    return int(load().bto_last_error(ctx))
+
+
+def bto_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def bto_destroy(ctx: int) -> None:
+    if ctx:
+        load().bto_destroy(ctx)
+
+
+class Context:
+    """Owning handle of a libbto context with torch-allocated outputs.
+
+    ``Context(extent, origin, spacing, stride, interval)`` for one block, or
+    ``Context.batch(extents, origins, spacings, strides, interval)``.
+    """
+
+    def __init__(self, extent, origin, spacing, stride, interval, _handle=None):
+        self.handle = _handle if _handle is not None else bto_create(extent, origin, spacing, stride, interval)
+        self.interval = int(interval)
+        self.P = bto_num_seeds(self.handle)
+        self.nb = bto_num_blocks(self.handle)
+
+    @classmethod
+    def batch(cls, extents, origins, spacings, strides, interval):
+        h = bto_batch_create(extents, origins, spacings, strides, interval)
+        return cls(None, None, None, None, interval, _handle=h)
+
+    def offsets(self):
+        return bto_batch_offsets(self.handle)
+
+    def set_layout(self, layout):
+        bto_set_field_layout(self.handle, layout)
+
+    def set_launch(self, threads, ppt, ctas_per_sm=0):
+        bto_set_launch(self.handle, threads, ppt, ctas_per_sm)
+
+    def launch(self):
+        return bto_get_launch(self.handle)
+
+    def advect(self, field, dt, stream=None):
+        bto_advect_cycle(self.handle, field, dt, stream)
+
+    def advect_batch(self, field_ptrs, dt, stream=None):
+        bto_batch_advect_cycle(self.handle, field_ptrs, dt, stream)
+
+    def interval_graph(self, field_table, dt, stream=None):
+        bto_launch_interval_graph(self.handle, field_table, dt, stream)
+
+    def alloc_outputs(self, device=None):
+        import torch
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        return {"seeds": torch.empty((self.P, 3), dtype=torch.float32, device=dev),
+                "ends": torch.empty((self.P, 3), dtype=torch.float32, device=dev),
+                "valid": torch.empty((self.P,), dtype=torch.uint8, device=dev),
+                "exit_cycle": torch.empty((self.P,), dtype=torch.int32, device=dev)}
+
+    def end_interval(self, out=None, stream=None):
+        out = out if out is not None else self.alloc_outputs()
+        bto_end_interval(self.handle, out["seeds"], out["ends"], out["valid"],
+                         out.get("exit_cycle"), stream)
+        return out
+
+    def copy_active(self, d_out, stream=None):
+        return bto_copy_active(self.handle, d_out, stream)
+
+    def check(self):
+        _check(bto_last_error(self.handle), "bto_last_error")
+
+    def close(self):
+        if self.handle:
+            bto_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

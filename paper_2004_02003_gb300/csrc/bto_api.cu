@@ -1,0 +1,439 @@
+// libbto host side: the C ABI declared in include/bto.h.
+//
+// A context owns, on one device:
+//   blocks   [nb] BlockDev          geometry of each block
+//   perm     [P] int32              lattice point of each list slot (Morton order)
+//   act[2]   [P] float4             active lists (ping-pong): xi (cell units), id bits
+//   term     [P] float4             termination record per canonical id: xi, cycle
+//   cnt      [3*nb] int32           live counts, a ring over cycle % 3
+//   work     [3] int32              chunk queues, a ring over cycle % 3
+// Cycle c reads act[c%2] and cnt[c%3], writes act[(c+1)%2] and cnt[(c+1)%3],
+// and zeroes cnt[(c+2)%3] and work[(c+1)%3] for the cycle after. No host
+// synchronisation happens on the per-cycle path.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bto.h"
+#include "bto_internal.h"
+
+using bto::BlockDev;
+
+struct bto_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int32_t nb = 0;
+    int64_t P = 0;
+    int32_t L = 0;            // cycles per interval
+    int32_t cycle = 0;        // cycles advanced in the current interval
+    int layout = bto::LAYOUT_F3;
+    int nt = 256, ppt = 2, ctas_per_sm = 0, grid = 0;
+    size_t dyn_smem = 0;
+    std::vector<BlockDev> blocks_h;
+    BlockDev *blocks = nullptr;
+    int32_t *perm = nullptr;
+    float4 *act[2] = {nullptr, nullptr};
+    float4 *term = nullptr;
+    int32_t *cnt = nullptr;
+    int32_t *work = nullptr;
+    bto_status sticky = BTO_OK;
+    // cached interval graph
+    cudaGraphExec_t gexec = nullptr;
+    const void *const *gtable = nullptr;
+    float gdt = 0.f;
+    int gshape[4] = {0, 0, 0, 0};
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+bto_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return BTO_OK;
+    return e == cudaErrorMemoryAllocation ? BTO_ERR_OOM : BTO_ERR_CUDA;
+}
+
+#define BTO_TRY(expr)                                     \
+    do {                                                  \
+        bto_status st__ = (expr);                         \
+        if (st__ != BTO_OK) return st__;                  \
+    } while (0)
+
+#define BTO_CUDA(expr)                                    \
+    do {                                                  \
+        cudaError_t e__ = (expr);                         \
+        if (e__ != cudaSuccess) {                         \
+            (void)cudaGetLastError();                     \
+            return cuda_status(e__);                      \
+        }                                                 \
+    } while (0)
+
+// Bits of a Morton code: every third bit, starting at bit 0.
+uint32_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return (uint32_t)v;
+}
+
+// Canonical lattice ids in Morton order of (jx, jy, jz).
+void morton_order(const int32_t S[3], int32_t *out) {
+    const int32_t m = std::max(S[0], std::max(S[1], S[2]));
+    int bits = 0;
+    while ((1 << bits) < m) ++bits;
+    const uint64_t ncode = 1ull << (3 * bits);
+    int64_t k = 0;
+    for (uint64_t code = 0; code < ncode; ++code) {
+        const uint32_t x = compact3(code), y = compact3(code >> 1), z = compact3(code >> 2);
+        if ((int32_t)x < S[0] && (int32_t)y < S[1] && (int32_t)z < S[2])
+            out[k++] = (int32_t)x + S[0] * ((int32_t)y + S[1] * (int32_t)z);
+    }
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+void free_ctx(bto_ctx *c) {
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    cudaFree(c->blocks);
+    cudaFree(c->perm);
+    cudaFree(c->act[0]);
+    cudaFree(c->act[1]);
+    cudaFree(c->term);
+    cudaFree(c->cnt);
+    cudaFree(c->work);
+    delete c;
+}
+
+int chunk_size(const bto_ctx *c) { return c->nt * c->ppt; }
+
+bto_status configure_launch(bto_ctx *c) {
+    const bool batched = c->nb > 1;
+    c->dyn_smem = batched ? (size_t)(c->nb + 1) * sizeof(int) : 0;
+    int occ = 0;
+    BTO_CUDA(bto::advect_occupancy(c->layout, c->nt, c->ppt, batched, c->dyn_smem, &occ));
+    if (occ < 1) return BTO_ERR_UNSUPPORTED;
+    const int per_sm = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
+    // Enough CTAs to fill every SM, never more than there are chunks.
+    const int64_t chunks = (c->P + chunk_size(c) - 1) / chunk_size(c);
+    c->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * per_sm, chunks));
+    return BTO_OK;
+}
+
+void drop_graph(bto_ctx *c) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+}
+
+bto_status seed(bto_ctx *c, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->sm_count * 8);
+    BTO_CUDA(bto::launch_seed(c->blocks, c->nb, c->perm, c->P, c->act[0], c->cnt, c->cnt + c->nb,
+                              c->work, std::max(grid, 1), s));
+    c->cycle = 0;
+    return BTO_OK;
+}
+
+bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
+                       const float *spacings, const int32_t *strides, int32_t L, bto_ctx **out) {
+    if (!out || !extents || !origins || !spacings || !strides) return BTO_ERR_INVALID_ARG;
+    if (nb < 1 || nb > 8192 || L < 1) return BTO_ERR_INVALID_ARG;
+    std::vector<BlockDev> bl((size_t)nb);
+    int64_t P = 0;
+    for (int32_t b = 0; b < nb; ++b) {
+        BlockDev &B = bl[(size_t)b];
+        std::memset(&B, 0, sizeof(B));
+        int64_t nodes = 1;
+        const int32_t s = strides[b];
+        if (s < 1) return BTO_ERR_INVALID_ARG;
+        for (int a = 0; a < 3; ++a) {
+            const int32_t n = extents[3 * b + a];
+            const float o = origins[3 * b + a], h = spacings[3 * b + a];
+            if (n < 1 || !std::isfinite(o) || !finite_pos(h)) return BTO_ERR_INVALID_ARG;
+            // cell coordinates must stay exact integers at every node
+            if (n > (1 << 24)) return BTO_ERR_INVALID_ARG;
+            B.n[a] = n;
+            B.nn[a] = n + 1;
+            B.S[a] = (n + s - 1) / s;
+            B.inv_h[a] = 1.0f / h;
+            B.origin[a] = o;
+            B.h[a] = h;
+            nodes *= (int64_t)(n + 1);
+        }
+        if (nodes > (1ll << 29)) return BTO_ERR_INVALID_ARG;
+        B.stride = s;
+        B.nseeds = (int64_t)B.S[0] * B.S[1] * B.S[2];
+        if (B.nseeds > (1ll << 30)) return BTO_ERR_INVALID_ARG;
+        B.base = P;
+        P += B.nseeds;
+    }
+    if (P > (1ll << 31) - 1) return BTO_ERR_INVALID_ARG;
+
+    bto_ctx *c = new (std::nothrow) bto_ctx();
+    if (!c) return BTO_ERR_OOM;
+    c->nb = nb;
+    c->P = P;
+    c->L = L;
+    c->blocks_h = bl;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); free_ctx(c); return cuda_status(e); }
+
+    std::vector<int32_t> perm((size_t)P);
+    for (int32_t b = 0; b < nb; ++b) morton_order(bl[(size_t)b].S, perm.data() + bl[(size_t)b].base);
+
+    e = cudaMalloc(&c->blocks, sizeof(BlockDev) * (size_t)nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->act[0], sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->act[1], sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->cnt, sizeof(int32_t) * 3 * (size_t)nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(int32_t) * 3);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->blocks, bl.data(), sizeof(BlockDev) * (size_t)nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->perm, perm.data(), sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice);
+    // term records start as "not terminated" (w = -1: all bits set)
+    if (e == cudaSuccess) e = cudaMemset(c->term, 0xff, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMemset(c->cnt, 0, sizeof(int32_t) * 3 * (size_t)nb);
+    if (e == cudaSuccess) e = cudaMemset(c->work, 0, sizeof(int32_t) * 3);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); free_ctx(c); return cuda_status(e); }
+
+    bto_status st = configure_launch(c);
+    if (st == BTO_OK) st = seed(c, 0);
+    if (st == BTO_OK) st = cuda_status(cudaDeviceSynchronize());
+    if (st != BTO_OK) { (void)cudaGetLastError(); free_ctx(c); return st; }
+    *out = c;
+    return BTO_OK;
+}
+
+bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields, float dt,
+                       cudaStream_t s) {
+    if (!std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
+    if (c->cycle >= c->L) return BTO_ERR_STATE;
+    const int cyc = c->cycle;
+    bto::AdvectArgs a;
+    a.blocks = c->blocks;
+    a.nb = c->nb;
+    a.cycle = cyc;
+    a.field = field;
+    a.fields = fields;
+    a.in = c->act[cyc & 1];
+    a.out = c->act[(cyc + 1) & 1];
+    a.cnt_in = c->cnt + (size_t)(cyc % 3) * c->nb;
+    a.cnt_out = c->cnt + (size_t)((cyc + 1) % 3) * c->nb;
+    a.cnt_zero = c->cnt + (size_t)((cyc + 2) % 3) * c->nb;
+    a.work = c->work + (cyc % 3);
+    a.work_zero = c->work + ((cyc + 1) % 3);
+    a.term = c->term;
+    a.dt = dt;
+    cudaError_t e = bto::launch_advect(a, c->layout, c->nt, c->ppt, c->grid, c->dyn_smem, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->sticky = cuda_status(e);
+        return c->sticky;
+    }
+    c->cycle = cyc + 1;
+    return BTO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bto_status bto_create(const int32_t extent_cells[3], const float origin[3], const float spacing[3],
+                      int32_t seed_stride, int32_t interval_cycles, bto_ctx **out) {
+    if (!extent_cells || !origin || !spacing) return BTO_ERR_INVALID_ARG;
+    return create_impl(1, extent_cells, origin, spacing, &seed_stride, interval_cycles, out);
+}
+
+bto_status bto_batch_create(int32_t nb, const int32_t *extents, const float *origins,
+                            const float *spacings, const int32_t *strides,
+                            int32_t interval_cycles, bto_ctx **out) {
+    return create_impl(nb, extents, origins, spacings, strides, interval_cycles, out);
+}
+
+bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout) {
+    if (!ctx) return BTO_ERR_INVALID_ARG;
+    if (layout != BTO_FIELD_F3_AOS && layout != BTO_FIELD_F4_AOS) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    const int old = ctx->layout;
+    ctx->layout = layout == BTO_FIELD_F4_AOS ? bto::LAYOUT_F4 : bto::LAYOUT_F3;
+    bto_status st = configure_launch(ctx);
+    if (st != BTO_OK) { ctx->layout = old; configure_launch(ctx); return st; }
+    drop_graph(ctx);
+    return BTO_OK;
+}
+
+int64_t bto_num_seeds(const bto_ctx *ctx) { return ctx ? ctx->P : -1; }
+
+int32_t bto_num_blocks(const bto_ctx *ctx) { return ctx ? ctx->nb : -1; }
+
+bto_status bto_batch_offsets(const bto_ctx *ctx, int64_t *offsets) {
+    if (!ctx || !offsets) return BTO_ERR_INVALID_ARG;
+    for (int32_t b = 0; b < ctx->nb; ++b) offsets[b] = ctx->blocks_h[(size_t)b].base;
+    offsets[ctx->nb] = ctx->P;
+    return BTO_OK;
+}
+
+bto_status bto_advect_cycle(bto_ctx *ctx, const void *d_field, float dt, bto_stream stream) {
+    if (!ctx || !d_field) return BTO_ERR_INVALID_ARG;
+    if (ctx->nb != 1) return BTO_ERR_STATE;
+    const uintptr_t align = ctx->layout == bto::LAYOUT_F4 ? 16 : 4;
+    if (reinterpret_cast<uintptr_t>(d_field) % align) return BTO_ERR_INVALID_ARG;
+    return advect_impl(ctx, d_field, nullptr, dt, (cudaStream_t)stream);
+}
+
+bto_status bto_batch_advect_cycle(bto_ctx *ctx, const void *const *d_fields, float dt,
+                                  bto_stream stream) {
+    if (!ctx || !d_fields) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_fields) % alignof(void *)) return BTO_ERR_INVALID_ARG;
+    return advect_impl(ctx, nullptr, d_fields, dt, (cudaStream_t)stream);
+}
+
+bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_table, float dt,
+                                     bto_stream stream) {
+    if (!ctx || !d_field_table || !std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_field_table) % alignof(void *)) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    const bool same = ctx->gexec && ctx->gtable == d_field_table && ctx->gdt == dt &&
+                      ctx->gshape[0] == ctx->layout && ctx->gshape[1] == ctx->nt &&
+                      ctx->gshape[2] == ctx->ppt && ctx->gshape[3] == ctx->grid;
+    if (!same) {
+        drop_graph(ctx);
+        if (!ctx->capture_stream)
+            BTO_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        BTO_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        bto_status st = BTO_OK;
+        for (int32_t c = 0; c < ctx->L && st == BTO_OK; ++c)
+            st = advect_impl(ctx, nullptr, d_field_table + (size_t)c * ctx->nb, dt,
+                             ctx->capture_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        ctx->cycle = 0;
+        if (st != BTO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            ctx->gexec = nullptr;
+            return cuda_status(e);
+        }
+        ctx->gtable = d_field_table;
+        ctx->gdt = dt;
+        ctx->gshape[0] = ctx->layout;
+        ctx->gshape[1] = ctx->nt;
+        ctx->gshape[2] = ctx->ppt;
+        ctx->gshape[3] = ctx->grid;
+    }
+    BTO_CUDA(cudaGraphLaunch(ctx->gexec, (cudaStream_t)stream));
+    ctx->cycle = ctx->L;
+    return BTO_OK;
+}
+
+bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t *d_valid,
+                            int32_t *d_exit_cycle, bto_stream stream) {
+    if (!ctx || !d_seeds || !d_ends || !d_valid) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_seeds) % 4 || reinterpret_cast<uintptr_t>(d_ends) % 4 ||
+        reinterpret_cast<uintptr_t>(d_exit_cycle) % 4)
+        return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != ctx->L) return BTO_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = ctx->L;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((ctx->P + 255) / 256, (int64_t)ctx->sm_count * 8));
+    BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->nb, ctx->act[L & 1],
+                                    ctx->cnt + (size_t)(L % 3) * ctx->nb, ctx->P, d_ends, d_valid,
+                                    d_exit_cycle, grid, s));
+    BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
+                                    d_valid, d_exit_cycle, grid, s));
+    return seed(ctx, s);
+}
+
+bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta, int32_t particles_per_thread,
+                          int32_t ctas_per_sm) {
+    if (!ctx) return BTO_ERR_INVALID_ARG;
+    if (threads_per_cta != 128 && threads_per_cta != 256) return BTO_ERR_INVALID_ARG;
+    if (particles_per_thread != 1 && particles_per_thread != 2 && particles_per_thread != 4)
+        return BTO_ERR_INVALID_ARG;
+    if (ctas_per_sm < 0 || ctas_per_sm > 64) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    const int o[3] = {ctx->nt, ctx->ppt, ctx->ctas_per_sm};
+    ctx->nt = threads_per_cta;
+    ctx->ppt = particles_per_thread;
+    ctx->ctas_per_sm = ctas_per_sm;
+    bto_status st = configure_launch(ctx);
+    if (st != BTO_OK) {
+        ctx->nt = o[0]; ctx->ppt = o[1]; ctx->ctas_per_sm = o[2];
+        configure_launch(ctx);
+        return st;
+    }
+    drop_graph(ctx);
+    return BTO_OK;
+}
+
+bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[4]) {
+    if (!ctx || !out) return BTO_ERR_INVALID_ARG;
+    out[0] = ctx->nt;
+    out[1] = ctx->ppt;
+    out[2] = ctx->ctas_per_sm;
+    out[3] = ctx->grid;
+    return BTO_OK;
+}
+
+bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream stream) {
+    if (!ctx || !d_out || !live) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_out) % 16) return BTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cyc = ctx->cycle;
+    BTO_CUDA(cudaMemcpyAsync(d_out, ctx->act[cyc & 1], sizeof(float4) * (size_t)ctx->P,
+                             cudaMemcpyDeviceToDevice, s));
+    BTO_CUDA(cudaMemcpyAsync(live, ctx->cnt + (size_t)(cyc % 3) * ctx->nb,
+                             sizeof(int32_t) * (size_t)ctx->nb, cudaMemcpyDeviceToHost, s));
+    BTO_CUDA(cudaStreamSynchronize(s));
+    return BTO_OK;
+}
+
+bto_status bto_last_error(bto_ctx *ctx) {
+    if (!ctx) return BTO_ERR_INVALID_ARG;
+    bto_status st = ctx->sticky;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (st == BTO_OK && e != cudaSuccess) st = cuda_status(e);
+    ctx->sticky = BTO_OK;
+    return st;
+}
+
+const char *bto_status_string(bto_status s) {
+    switch (s) {
+        case BTO_OK: return "ok";
+        case BTO_ERR_INVALID_ARG: return "invalid argument";
+        case BTO_ERR_STATE: return "call out of order for the interval state";
+        case BTO_ERR_CUDA: return "CUDA error";
+        case BTO_ERR_OOM: return "out of memory";
+        case BTO_ERR_TIMEOUT: return "bounded device wait timed out";
+        case BTO_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+void bto_destroy(bto_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal declarations shared by the host API (bto_api.cu) and the kernels
+// (bto_kernels.cu) of libbto. Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bto {
+
+// One block of the uniform grid, as the kernels see it. Positions inside the
+// library are block-local CELL coordinates xi = (x - origin) / h, so node i
+// sits at xi = i and the block is the closed box [0, n].
+struct BlockDev {
+    int32_t n[3];       // cells per axis
+    int32_t nn[3];      // nodes per axis (n + 1)
+    int32_t S[3];       // seed lattice size per axis, ceil(n / stride)
+    int32_t stride;     // seed stride in cells
+    float inv_h[3];     // 1 / spacing
+    float origin[3];    // physical position of node (0,0,0)
+    float h[3];         // spacing
+    int32_t pad_;
+    int64_t base;       // first canonical id of the block == first slot of its list region
+    int64_t nseeds;     // seeds of the block
+};
+
+// Arguments of one advection cycle (kernel K3: RK4 + termination + compaction).
+struct AdvectArgs {
+    const BlockDev *blocks;      // [nb] device
+    int32_t nb;
+    int32_t cycle;               // cycle index within the interval
+    const void *field;           // single field pointer (nb == 1 calls), or NULL
+    const void *const *fields;   // device array [nb] used when field == NULL
+    const float4 *in;            // active list at cycle start (xi, id bits)
+    float4 *out;                 // active list after the cycle
+    const int32_t *cnt_in;       // [nb] live particles at cycle start
+    int32_t *cnt_out;            // [nb] survivors (zero on entry)
+    int32_t *cnt_zero;           // [nb] zeroed here: the next cycle's output counts
+    int32_t *work;               // chunk queue of this cycle (zero on entry)
+    int32_t *work_zero;          // zeroed here: the next cycle's chunk queue
+    float4 *term;                // [P] termination record per canonical id
+    float dt;
+};
+
+enum { LAYOUT_F3 = 0, LAYOUT_F4 = 1 };
+
+// Kernel launchers (bto_kernels.cu). Each returns cudaGetLastError().
+cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, int grid,
+                          size_t dyn_smem, cudaStream_t s);
+cudaError_t advect_occupancy(int layout, int nt, int ppt, bool batched, size_t dyn_smem,
+                             int *ctas_per_sm);
+cudaError_t launch_seed(const BlockDev *blocks, int32_t nb, const int32_t *perm, int64_t P,
+                        float4 *act, int32_t *cnt0, int32_t *cnt1, int32_t *work0,
+                        int grid, cudaStream_t s);
+cudaError_t launch_write_live(const BlockDev *blocks, int32_t nb, const float4 *act,
+                              const int32_t *cnt, int64_t P, float *ends, uint8_t *valid,
+                              int32_t *exit_cycle, int grid, cudaStream_t s);
+cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,
+                              float *seeds, float *ends, uint8_t *valid, int32_t *exit_cycle,
+                              int grid, cudaStream_t s);
+
+}  // namespace bto

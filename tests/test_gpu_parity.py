@@ -1,0 +1,358 @@
+"""GPU path (through the C ABI) against the FP64 oracle and closed forms."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_02003_gb300 import bto, inputs
+
+from gpu_helpers import block_views, compare, run_gpu_interval, to_f4
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    from paper_2004_02003_gb300 import build
+    build.build()
+    bto.load()
+    import torch
+    torch.cuda.set_device(0)
+    yield
+
+
+def _dev(arrs):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+# ----------------------------------------------------------------------------
+# ABC block: 32^3 cells over [0,1]^3, stride 2 (4096 seeds), 50 cycles, dt 0.01
+# ----------------------------------------------------------------------------
+N1, H1, S1, L1, DT1 = (32, 32, 32), (1.0 / 32,) * 3, 2, 50, 0.01
+
+
+@pytest.fixture(scope="module")
+def abc_case():
+    fields = [inputs.abc_field(N1, (0, 0, 0), H1, c * DT1) for c in range(L1)]
+    ref = oracle.run_interval(oracle.Grid.make(N1, (0, 0, 0), H1), S1, L1, DT1, lambda c: fields[c])
+    return fields, ref
+
+
+def test_abc_block_parity_f3(abc_case):
+    fields, ref = abc_case
+    ctx = bto.Context(N1, (0, 0, 0), H1, S1, L1)
+    gpu = run_gpu_interval(ctx, _dev(fields), DT1)
+    rep = compare(gpu, ref, H1)
+    assert rep["n"] == 4096 and rep["both_valid"] > 0
+    ctx.close()
+
+
+def test_abc_block_f4_layout_is_bitwise_f3(abc_case):
+    fields, _ = abc_case
+    a = bto.Context(N1, (0, 0, 0), H1, S1, L1)
+    ga = run_gpu_interval(a, _dev(fields), DT1)
+    b = bto.Context(N1, (0, 0, 0), H1, S1, L1)
+    b.set_layout(bto.BTO_FIELD_F4_AOS)
+    gb = run_gpu_interval(b, _dev([to_f4(f) for f in fields]), DT1)   # NaN pad must be ignored
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k], equal_nan=True), k
+    a.close(); b.close()
+
+
+@pytest.mark.parametrize("layout", [bto.BTO_FIELD_F3_AOS, bto.BTO_FIELD_F4_AOS])
+def test_launch_shapes_give_identical_results(abc_case, layout):
+    fields, _ = abc_case
+    devf = _dev(fields if layout == bto.BTO_FIELD_F3_AOS else [to_f4(f) for f in fields])
+    results = []
+    for nt in (128, 256):
+        for ppt in (1, 2, 4):
+            for cps in (0, 1):
+                ctx = bto.Context(N1, (0, 0, 0), H1, S1, L1)
+                ctx.set_layout(layout)
+                ctx.set_launch(nt, ppt, cps)
+                results.append(run_gpu_interval(ctx, devf, DT1))
+                ctx.close()
+    for r in results[1:]:
+        for k in r:
+            assert np.array_equal(r[k], results[0][k]), k
+
+
+# ----------------------------------------------------------------------------
+# Ragged block: odd extents, stride 2 with ceil, offset origin, anisotropic h
+# ----------------------------------------------------------------------------
+def test_ragged_block_turbulence_parity():
+    n, origin, h, s, L = (45, 37, 29), (-0.3, 0.7, 1.1), (0.02, 0.025, 0.03), 2, 40
+    modes = inputs.fourier_modes(7, m=16, kmax=6.0)
+    fields = [inputs.fourier_field(modes, n, origin, h, c) for c in range(L)]
+    dt = 0.3 * min(h)                          # <= 0.3 cells per step (|u| <= ~1)
+    g = oracle.Grid.make(n, origin, h)
+    ref = oracle.run_interval(g, s, L, dt, lambda c: fields[c])
+    ctx = bto.Context(n, origin, h, s, L)
+    assert ctx.P == 23 * 19 * 15
+    gpu = run_gpu_interval(ctx, _dev(fields), dt)
+    rep = compare(gpu, ref, h)
+    assert 0 < rep["valid"] < rep["n"]         # some terminate, some survive
+    ctx.close()
+
+
+def test_two_intervals_reseed_and_continue():
+    n, h, s, L = (24, 20, 16), (0.05, 0.05, 0.05), 1, 12
+    modes = inputs.fourier_modes(11, m=12, kmax=4.0)
+    fields = [inputs.fourier_field(modes, n, (0, 0, 0), h, c) for c in range(2 * L)]
+    dt = 0.4 * 0.05
+    g = oracle.Grid.make(n, (0, 0, 0), h)
+    ctx = bto.Context(n, (0, 0, 0), h, s, L)
+    devf = _dev(fields)
+    for k in range(2):
+        gpu = run_gpu_interval(ctx, devf[k * L:(k + 1) * L], dt)
+        ref = oracle.run_interval(g, s, L, dt, lambda c: fields[c], c0=k * L)
+        compare(gpu, ref, h)
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# Closed forms on the GPU path
+# ----------------------------------------------------------------------------
+def test_uniform_translation_gpu():
+    n, h, s, L, dt = (16, 16, 16), (1.0 / 16,) * 3, 4, 20, 0.5
+    c = np.array([0.0078125, -0.00390625, 0.001953125])
+    ctx = bto.Context(n, (0, 0, 0), h, s, L)
+    gpu = run_gpu_interval(ctx, _dev([inputs.uniform_field(n, c)] * L), dt)
+    x0 = gpu["seeds"].astype(np.float64)
+    want = x0 + L * dt * c
+    inside = np.all((want >= 0) & (want <= 1), axis=1)
+    assert np.array_equal(gpu["valid"] == 1, inside)
+    assert np.max(np.abs(gpu["ends"][inside] - want[inside]) * 16) < 1e-4
+    ctx.close()
+
+
+def test_affine_field_gpu_matches_rk4_closed_form():
+    A = np.array([[-0.75, 1.5, 0.25], [-1.25, 0.5, -0.5], [0.375, -0.25, -1.0]])
+    b = np.array([0.5, -0.25, 0.125])
+    n, h, origin, s, L, dt = (64, 64, 64), (0.25,) * 3, (-8.0,) * 3, 8, 12, 0.0625
+    ctx = bto.Context(n, origin, h, s, L)
+    gpu = run_gpu_interval(ctx, _dev([inputs.affine_field(n, origin, h, A, b)] * L), dt)
+    Z = dt * A
+    M = np.eye(3) + Z / 2 + Z @ Z / 6 + Z @ Z @ Z / 24
+    x = gpu["seeds"].astype(np.float64)
+    for _ in range(L):
+        x = x + dt * (x @ A.T + b) @ M.T
+    ok = gpu["valid"] == 1
+    far = np.all((x > -7.5) & (x < 7.5), axis=1)
+    assert np.all(ok[far])
+    assert np.max(np.abs(gpu["ends"][far] - x[far]) / 0.25) < 1e-4
+    ctx.close()
+
+
+def test_straight_line_exit_cycles_gpu_brute_force():
+    n, h, s, L, dt = (20, 20, 20), (0.05,) * 3, 1, 30, 0.0099
+    vel = (1.0, -0.5, 0.25)
+    ctx = bto.Context(n, (0, 0, 0), h, s, L)
+    gpu = run_gpu_interval(ctx, _dev([inputs.uniform_field(n, vel)] * L), dt)
+    seeds = oracle.seeds(oracle.Grid.make(n, (0, 0, 0), h), s)
+    step = [Fraction(v) * Fraction(dt) for v in vel]
+    for p in range(seeds.shape[0]):
+        x = [Fraction(v) for v in seeds[p]]
+        want = -1
+        for c in range(L):
+            nxt = [x[a] + step[a] for a in range(3)]
+            if any(not (0 <= v <= 1) for v in nxt):
+                want = c
+                break
+            x = nxt
+        assert gpu["exit_cycle"][p] == want, p
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# Degenerate cases and contract
+# ----------------------------------------------------------------------------
+def test_zero_dt_is_a_no_op():
+    n, h = (8, 8, 8), (0.125,) * 3
+    ctx = bto.Context(n, (0, 0, 0), h, 1, 3)
+    f = inputs.abc_field(n, (0, 0, 0), h, 0.0)
+    gpu = run_gpu_interval(ctx, _dev([f] * 3), 0.0)
+    assert np.all(gpu["valid"] == 1)
+    assert np.array_equal(gpu["ends"], gpu["seeds"])
+    ctx.close()
+
+
+def test_single_cell_single_seed_and_backward_dt():
+    f = np.zeros((2, 2, 2, 3), dtype=np.float32)
+    f[..., 0] = -1.0
+    ctx = bto.Context((1, 1, 1), (0, 0, 0), (1, 1, 1), 5, 2)
+    assert ctx.P == 1
+    gpu = run_gpu_interval(ctx, _dev([f, f]), -0.25)     # backward: moves +x
+    assert gpu["valid"][0] == 1
+    assert np.allclose(gpu["ends"][0], [0.5, 0.0, 0.0])
+    ctx.close()
+
+
+def test_nan_field_terminates_and_matches_oracle():
+    n, h, L, dt = (6, 6, 6), (1.0, 1.0, 1.0), 2, 0.1
+    f = np.ones((7, 7, 7, 3), dtype=np.float32) * 0.5
+    f[3, 3, 3] = np.nan
+    ctx = bto.Context(n, (0, 0, 0), h, 1, L)
+    gpu = run_gpu_interval(ctx, _dev([f, f]), dt)
+    ref = oracle.run_interval(oracle.Grid.make(n, (0, 0, 0), h), 1, L, dt, lambda c: f)
+    assert np.array_equal(gpu["valid"], ref.valid)
+    assert (gpu["valid"] == 0).sum() > 0
+    ctx.close()
+
+
+def test_call_order_and_argument_errors():
+    import torch
+    n, h = (4, 4, 4), (0.25,) * 3
+    ctx = bto.Context(n, (0, 0, 0), h, 1, 2)
+    f = torch.zeros((5, 5, 5, 3), dtype=torch.float32, device="cuda")
+    out = ctx.alloc_outputs()
+    with pytest.raises(bto.BtoError) as e:
+        ctx.end_interval(out)
+    assert e.value.status == bto.BTO_ERR_STATE
+    ctx.advect(f, 0.1)
+    with pytest.raises(bto.BtoError) as e:
+        ctx.set_layout(bto.BTO_FIELD_F4_AOS)
+    assert e.value.status == bto.BTO_ERR_STATE
+    ctx.advect(f, 0.1)
+    with pytest.raises(bto.BtoError) as e:
+        ctx.advect(f, 0.1)
+    assert e.value.status == bto.BTO_ERR_STATE
+    with pytest.raises(bto.BtoError) as e:
+        ctx.advect(f, float("nan"))
+    assert e.value.status == bto.BTO_ERR_INVALID_ARG
+    ctx.end_interval(out)
+    ctx.set_layout(bto.BTO_FIELD_F4_AOS)
+    g = torch.zeros(5 * 5 * 5 * 4 + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(bto.BtoError) as e:
+        ctx.advect(g[1:].data_ptr(), 0.1)               # not 16-byte aligned
+    assert e.value.status == bto.BTO_ERR_INVALID_ARG
+    assert ctx.launch()["grid"] >= 1
+    ctx.check()
+    ctx.close()
+
+
+def test_every_output_entry_written_once():
+    import torch
+    n, h, L, dt = (30, 30, 30), (1.0 / 30,) * 3, 20, 0.02
+    fields = [inputs.abc_field(n, (0, 0, 0), h, c * dt) for c in range(L)]
+    ctx = bto.Context(n, (0, 0, 0), h, 2, L)
+    out = ctx.alloc_outputs()
+    out["seeds"].fill_(float("nan")); out["ends"].fill_(float("nan"))
+    out["valid"].fill_(7); out["exit_cycle"].fill_(-99)
+    for f in _dev(fields):
+        ctx.advect(f, dt)
+    ctx.end_interval(out)
+    torch.cuda.synchronize()
+    v = out["valid"].cpu().numpy()
+    e = out["exit_cycle"].cpu().numpy()
+    assert set(np.unique(v)) <= {0, 1}
+    assert np.all((e == -1) == (v == 1)) and np.all(e[v == 0] >= 0) and np.all(e < L)
+    assert torch.isfinite(out["ends"]).all() and torch.isfinite(out["seeds"]).all()
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# Batched blocks, interval graph, global map
+# ----------------------------------------------------------------------------
+def _uneven_blocks():
+    ext = [(16, 24, 20), (33, 17, 9), (8, 8, 40), (27, 27, 27), (5, 3, 2)]
+    strides = [1, 2, 4, 3, 1]
+    origins = [(0.1 * b, -0.2 * b, 0.05 * b) for b in range(len(ext))]
+    spac = [(0.02, 0.03, 0.025), (0.04, 0.02, 0.05), (0.03, 0.03, 0.01), (0.02, 0.02, 0.02),
+            (0.1, 0.1, 0.1)]
+    return ext, origins, spac, strides
+
+
+def test_batched_equals_single_blocks_and_oracle():
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt = 16, 0.006
+    modes = inputs.fourier_modes(5, m=16, kmax=5.0)
+    fields = [[inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(len(ext))]
+              for c in range(L)]
+    devf = [_dev(fc) for fc in fields]
+    ptrs = [torch.tensor([t.data_ptr() for t in fc], dtype=torch.int64, device="cuda") for fc in devf]
+    bctx = bto.Context.batch(ext, origins, spac, strides, L)
+    off = bctx.offsets()
+    for c in range(L):
+        bctx.advect_batch(ptrs[c], dt)
+    out = bctx.end_interval()
+    bctx.check()
+    torch.cuda.synchronize()
+    bout = {k: v.cpu().numpy() for k, v in out.items()}
+    for b in range(len(ext)):
+        ctx = bto.Context(ext[b], origins[b], spac[b], strides[b], L)
+        single = run_gpu_interval(ctx, [devf[c][b] for c in range(L)], dt)
+        ctx.close()
+        for k in single:
+            assert np.array_equal(single[k], bout[k][off[b]:off[b + 1]]), (b, k)
+        ref = oracle.run_interval(oracle.Grid.make(ext[b], origins[b], spac[b]), strides[b], L, dt,
+                                  lambda c: fields[c][b])
+        compare(single, ref, spac[b])
+    bctx.close()
+
+
+def test_interval_graph_equals_per_cycle_calls():
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt = 8, 0.006
+    modes = inputs.fourier_modes(6, m=8, kmax=5.0)
+    devf = [_dev([inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(len(ext))])
+            for c in range(L)]
+    table = torch.tensor([t.data_ptr() for fc in devf for t in fc], dtype=torch.int64, device="cuda")
+    nb = len(ext)
+    a = bto.Context.batch(ext, origins, spac, strides, L)
+    for c in range(L):
+        a.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    ra = {k: v.cpu().numpy() for k, v in a.end_interval().items()}
+    b = bto.Context.batch(ext, origins, spac, strides, L)
+    for rep in range(2):                               # capture, then relaunch
+        b.interval_graph(table, dt)
+        rb = {k: v.cpu().numpy() for k, v in b.end_interval().items()}
+        for k in ra:
+            assert np.array_equal(ra[k], rb[k]), (rep, k)
+    a.check(); b.check()
+    a.close(); b.close()
+
+
+def test_bto_valid_ends_equal_global_map():
+    # BTO blocks vs one block over the whole domain (particles cross blocks):
+    # a particle that stays in its block follows the same cells and node values.
+    import torch
+    nbx, n, L = 2, 24, 30
+    G = nbx * n
+    h = (1.0 / G,) * 3
+    modes = inputs.fourier_modes(9, m=24, kmax=8.0)
+    dt = 0.25 * h[0]
+    gfields = [inputs.fourier_field(modes, (G, G, G), (0, 0, 0), h, c) for c in range(L)]
+    blocks = [block_views(f, (nbx,) * 3, (n, n, n)) for f in gfields]
+    ext = [(n, n, n)] * nbx ** 3
+    origins = [(bx * n * h[0], by * n * h[0], bz * n * h[0])
+               for bz in range(nbx) for by in range(nbx) for bx in range(nbx)]
+    bctx = bto.Context.batch(ext, origins, [h] * len(ext), [2] * len(ext), L)
+    dev = [_dev(bc) for bc in blocks]
+    ptrs = [torch.tensor([t.data_ptr() for t in fc], dtype=torch.int64, device="cuda") for fc in dev]
+    for c in range(L):
+        bctx.advect_batch(ptrs[c], dt)
+    bo = {k: v.cpu().numpy() for k, v in bctx.end_interval().items()}
+    gctx = bto.Context((G, G, G), (0, 0, 0), h, 2, L)
+    go = run_gpu_interval(gctx, _dev(gfields), dt)
+    # map each block seed to its global canonical id
+    S = n // 2
+    gid = []
+    for bz in range(nbx):
+        for by in range(nbx):
+            for bx in range(nbx):
+                j = np.arange(S ** 3)
+                jx, jy, jz = j % S + bx * S, (j // S) % S + by * S, j // (S * S) + bz * S
+                gid.append(jx + G // 2 * (jy + G // 2 * jz))
+    gid = np.concatenate(gid)
+    assert np.max(np.abs(bo["seeds"] - go["seeds"][gid]) / h[0]) < 1e-5
+    v = bo["valid"] == 1
+    assert np.all(go["valid"][gid][v] == 1)
+    assert np.max(np.abs(bo["ends"][v] - go["ends"][gid][v]) / h[0]) < 1e-4
+    frac = 1.0 - v.mean()
+    assert 0.0 < frac < 0.6
+    bctx.close(); gctx.close()
