@@ -52,11 +52,17 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/graph/global-map/e2e legs")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--layout", default="f3", choices=["f3", "f4"],
+                    help="field layout handed to the library (f4 pads each node to 16 bytes)")
+    ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
+    ap.add_argument("--fields", type=int, default=INTERVAL,
+                    help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
+                         "fewer fields make a small case for profiling")
     return ap.parse_args()
 
 
@@ -107,7 +113,7 @@ def sum_over_ranks(v, world):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -120,7 +126,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -129,7 +135,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def __exit__(self, *a):
         if self.proc:
@@ -142,7 +151,13 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo, hi = getattr(self, "t_start", 0.0), getattr(self, "t_end", float("inf"))
+        inside = [ln for (t, ln) in self.lines if lo <= t <= hi + 0.05]
+        if not inside and self.lines:
+            # timed region shorter than the sampling period: nearest sample
+            mid = 0.5 * (lo + hi)
+            inside = [min(self.lines, key=lambda tl: abs(tl[0] - mid))[1]]
+        for ln in inside:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -262,11 +277,20 @@ def run_ours(args):
     blocks, ext, org, spc = block_layout()
     nb = len(blocks)
     L = INTERVAL
-    fields, gfields = synth_fields(modes, blocks, L, dev, with_global=(rank == 0 and not args.no_extras))
+    nf = max(1, min(args.fields, L))
+    fields, gfields = synth_fields(modes, blocks, nf, dev, with_global=(rank == 0 and not args.no_extras))
+    if args.layout == "f4":
+        fields = [[torch.nn.functional.pad(f, (0, 1)).contiguous() for f in row] for row in fields]
+    fields = [fields[c % nf] for c in range(L)]
+    gfields = [gfields[c % nf] for c in range(L)] if gfields else gfields
     table = torch.tensor([f.data_ptr() for row in fields for f in row], dtype=torch.int64, device=dev)
     field_bytes_cycle = sum(f.numel() * 4 for f in fields[0])
 
     ctx = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+    layout = bto.BTO_FIELD_F4_AOS if args.layout == "f4" else bto.BTO_FIELD_F3_AOS
+    ctx.set_layout(layout)
+    if args.launch:
+        ctx.set_launch(*[int(v) for v in args.launch.split(",")])
     P = ctx.P
     out = ctx.alloc_outputs(dev)
 
@@ -306,13 +330,14 @@ def run_ours(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        time.sleep(0.3)            # let the sampler start before the timed region
+        clk.mark("t_start")
         t0.record(stream)
         for k in range(args.steps):
             one_step(ev)
-            if k == args.steps - 1:
-                pass
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.mark("t_end")
     barrier(world)
     elapsed = t0.elapsed_time(t1) / 1e3
     # per-launch durations of the last step (same work every step)
@@ -357,8 +382,8 @@ def run_ours(args):
             "workload": "turb256: 256^3 cells as 2x2x2 blocks of 128^3, Fourier turbulence (64 modes), "
                         "stride 2 (2,097,152 particles), interval 100, dt=0.25 cell/max|u|",
             "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
-            "field_layout": "F3_AOS", "field_bytes_per_cycle": field_bytes_cycle,
-            "l2": "inputs larger than L2: each cycle reads its own 206 MB field, 100 distinct fields per step",
+            "field_layout": args.layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
+            "l2": f"inputs larger than L2: each cycle reads a 206 MB field; {nf} distinct fields resident",
             "launch": ctx.launch(),
             "parallelism": f"weak: {world} rank(s), each the full workload, no collective",
         },
@@ -370,7 +395,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": frac,
                      "traffic": None, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": float(algo.mean()),
-                     "avg_launch_ms": float(np.mean(launch_ms))},
+                     "avg_launch_ms": float(np.mean(launch_ms)),
+                     "launch_ms_by_decile": [round(float(np.mean(launch_ms[k:k + L // 10])), 4)
+                                             for k in range(0, L, L // 10)]},
         "clocks": clk.summary(),
     }
 
@@ -378,13 +405,19 @@ def run_ours(args):
         res.update(extras(args, ctx, fields, gfields, table, out, exit_np, psteps, dt, dev, stream, rank, world,
                           ext, org, spc))
     if rank == 0 and world == 1:
-        res["cpu_baseline"] = cpu_baseline(fields, dt, args.cpu_seconds)
+        if args.cpu_seconds > 0:
+            res["cpu_baseline"] = cpu_baseline(fields, dt, args.cpu_seconds, org)
     ctx.close()
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ctx_layout(args):
+    from paper_2004_02003_gb300 import bto
+    return bto.BTO_FIELD_F4_AOS if args.layout == "f4" else bto.BTO_FIELD_F3_AOS
 
 
 def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, stream, rank, world, ext, org, spc):
@@ -395,6 +428,10 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     res = {}
     # (1) plain: one single-block context per block, one launch per block and cycle
     plain = [bto.Context(ext[b], org[b], spc[b], STRIDE, L) for b in range(nb)]
+    for p in plain:
+        p.set_layout(ctx_layout(args))
+        if args.launch:
+            p.set_launch(*[int(v) for v in args.launch.split(",")])
     outs = [p.alloc_outputs(dev) for p in plain]
 
     def plain_step():
@@ -419,6 +456,9 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
 
     # (2) graph: the interval's cycles as one CUDA graph
     g = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+    g.set_layout(ctx_layout(args))
+    if args.launch:
+        g.set_launch(*[int(v) for v in args.launch.split(",")])
     gout = g.alloc_outputs(dev)
     for _ in range(max(1, args.warmup)):
         g.interval_graph(table, dt)
@@ -533,30 +573,31 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, as it stands, on the host cores
 # ---------------------------------------------------------------------------
-def cpu_baseline(fields, dt, seconds, block=0):
+def cpu_baseline(fields, dt, seconds, org):
+    """The oracle on the same workload (every block, all 100 cycles), block
+    by block, until ``seconds`` of oracle time have been spent."""
     import oracle
     h = 1.0 / GLOBAL_CELLS
-    g = oracle.Grid.make((BLOCK_CELLS,) * 3, (0, 0, 0), (h, h, h))
-    return _time_oracle(g, fields, dt, seconds, block, oracle.max_threads())
-
-
-def _time_oracle(g, fields, dt, seconds, block, nthreads):
-    import oracle
-    st = oracle.State(oracle.seeds(g, STRIDE))
-    steps, spent, c = 0, 0.0, 0
-    while c < INTERVAL and spent < seconds:
-        f = fields[c][block]
-        f = f.cpu().numpy() if hasattr(f, "cpu") else f
-        live = int((st.exit_cycle < 0).sum())
-        t = time.perf_counter()
-        oracle.cycle(g, f, dt, c, st)
-        spent += time.perf_counter() - t
-        steps += live
-        c += 1
-    return {"value": steps / spent, "unit": "particle-steps/s", "cores": nthreads,
-            "host_cpus": os.cpu_count(), "kind": "oracle",
-            "sample": f"block 0 of 8 (262,144 particles), cycles 0..{c - 1} of 100 "
-                      f"({steps} particle-steps, {spent:.1f} s)"}
+    nthreads = oracle.max_threads()
+    steps, spent, done = 0, 0.0, []
+    for b in range(len(org)):
+        if spent >= seconds:
+            break
+        g = oracle.Grid.make((BLOCK_CELLS,) * 3, org[b], (h, h, h))
+        st = oracle.State(oracle.seeds(g, STRIDE))
+        c = 0
+        while c < INTERVAL and spent < seconds:
+            f = fields[c][b].cpu().numpy()
+            live = int((st.exit_cycle < 0).sum())
+            t = time.perf_counter()
+            oracle.cycle(g, f, dt, c, st)
+            spent += time.perf_counter() - t
+            steps += live
+            c += 1
+        done.append(f"block {b}: cycles 0..{c - 1}")
+    return {"value": steps / spent, "unit": "particle-steps/s", "cores": nthreads, "host_cpus": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"turb256 workload, {'; '.join(done)} ({steps} particle-steps, {spent:.1f} s of oracle time)"}
 
 
 def run_reference(args):

@@ -159,14 +159,19 @@ BTO_API bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_
                                      float dt, bto_stream stream);
 
 /* Launch shape of the advection kernel: threads per CTA (128 or 256),
- * particles per thread (1, 2 or 4) and CTAs per SM (0 = as many as fit).
- * Results do not depend on it. Between intervals only. */
+ * particles per thread (1, 2 or 4; a warp owns 32*ppt list slots), CTAs per
+ * SM (0 = as many as fit) and reg_cap (1 = registers capped at 64 per
+ * thread so that 1024 threads fit on an SM; 0 = no cap). Results do not
+ * depend on the shape. Only at cycle 0 (between intervals), else
+ * BTO_ERR_STATE; changing particles_per_thread reseeds the interval
+ * (synchronously). */
 BTO_API bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta,
-                          int32_t particles_per_thread, int32_t ctas_per_sm);
+                                  int32_t particles_per_thread, int32_t ctas_per_sm,
+                                  int32_t reg_cap);
 
 /* Report the launch shape in use (host ints: threads, ppt, ctas_per_sm,
- * grid size). */
-BTO_API bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[4]);
+ * reg_cap, grid size). */
+BTO_API bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]);
 
 /* Diagnostics (not for the per-cycle path): copy the active particle list as
  * it stands before the next cycle.

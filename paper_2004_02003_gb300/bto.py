@@ -55,7 +55,7 @@ def _declare(lib):
         "bto_batch_advect_cycle": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_end_interval": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_launch_interval_graph": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
-        "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
         "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
         "bto_last_error": ([vp], ctypes.c_int),
@@ -178,16 +178,17 @@ def bto_launch_interval_graph(ctx: int, d_field_table, dt: float, stream=None) -
            "bto_launch_interval_graph")
 
 
-def bto_set_launch(ctx: int, threads_per_cta: int, particles_per_thread: int, ctas_per_sm: int = 0) -> None:
-    _check(load().bto_set_launch(ctx, int(threads_per_cta), int(particles_per_thread), int(ctas_per_sm)),
-           "bto_set_launch")
+def bto_set_launch(ctx: int, threads_per_cta: int, particles_per_thread: int, ctas_per_sm: int = 0,
+                   reg_cap: int = 0) -> None:
+    _check(load().bto_set_launch(ctx, int(threads_per_cta), int(particles_per_thread), int(ctas_per_sm),
+                                 int(reg_cap)), "bto_set_launch")
 
 
 def bto_get_launch(ctx: int) -> dict:
-    buf = (ctypes.c_int32 * 4)()
+    buf = (ctypes.c_int32 * 5)()
     _check(load().bto_get_launch(ctx, buf), "bto_get_launch")
     return {"threads_per_cta": buf[0], "particles_per_thread": buf[1], "ctas_per_sm": buf[2],
-            "grid": buf[3]}
+            "reg_cap": buf[3], "grid": buf[4]}
 
 
 def bto_copy_active(ctx: int, d_out, stream=None) -> list:
@@ -234,8 +235,8 @@ class Context:
     def set_layout(self, layout):
         bto_set_field_layout(self.handle, layout)
 
-    def set_launch(self, threads, ppt, ctas_per_sm=0):
-        bto_set_launch(self.handle, threads, ppt, ctas_per_sm)
+    def set_launch(self, threads, ppt, ctas_per_sm=0, reg_cap=0):
+        bto_set_launch(self.handle, threads, ppt, ctas_per_sm, reg_cap)
 
     def launch(self):
         return bto_get_launch(self.handle)

@@ -2,13 +2,13 @@
 //
 // A context owns, on one device:
 //   blocks   [nb] BlockDev          geometry of each block
-//   perm     [P] int32              lattice point of each list slot (Morton order)
-//   act[2]   [P] float4             active lists (ping-pong): xi (cell units), id bits
+//   perm     [P] int32              lattice point of each Morton rank, per block
+//   gblock   [slots/32] int32       block of each 32-slot unit of the lists
+//   act[2]   [slots] float4         active lists (ping-pong): xi (cell units), id bits
+//   gcnt[2]  [slots/32] int32       live particles per group (ping-pong)
 //   term     [P] float4             termination record per canonical id: xi, cycle
-//   cnt      [3*nb] int32           live counts, a ring over cycle % 3
-//   work     [3] int32              chunk queues, a ring over cycle % 3
-// Cycle c reads act[c%2] and cnt[c%3], writes act[(c+1)%2] and cnt[(c+1)%3],
-// and zeroes cnt[(c+2)%3] and work[(c+1)%3] for the cycle after. No host
+// Each block's list region is its seed count rounded up to 128 slots. Cycle c
+// reads act[c%2], gcnt[c%2] and writes act[(c+1)%2], gcnt[(c+1)%2]. No host
 // synchronisation happens on the per-cycle path.
 #include <algorithm>
 #include <cmath>
@@ -29,24 +29,27 @@ struct bto_ctx {
     int sm_count = 0;
     int32_t nb = 0;
     int64_t P = 0;
+    int64_t slots = 0;        // list slots (regions rounded up to kRegionAlign)
     int32_t L = 0;            // cycles per interval
     int32_t cycle = 0;        // cycles advanced in the current interval
     int layout = bto::LAYOUT_F3;
-    int nt = 256, ppt = 2, ctas_per_sm = 0, grid = 0;
+    int nt = 128, ppt = 2, ctas_per_sm = 0, grid = 0;
+    bool cap = false;         // cap registers at 64 (1024 threads per SM)
     size_t dyn_smem = 0;
     std::vector<BlockDev> blocks_h;
     BlockDev *blocks = nullptr;
     int32_t *perm = nullptr;
+    int32_t *gblock = nullptr;
     float4 *act[2] = {nullptr, nullptr};
+    int32_t *gcnt[2] = {nullptr, nullptr};
     float4 *term = nullptr;
-    int32_t *cnt = nullptr;
-    int32_t *work = nullptr;
+    int64_t *diag_dst = nullptr;   // bto_copy_active scratch
     bto_status sticky = BTO_OK;
     // cached interval graph
     cudaGraphExec_t gexec = nullptr;
     const void *const *gtable = nullptr;
     float gdt = 0.f;
-    int gshape[4] = {0, 0, 0, 0};
+    int gshape[5] = {0, 0, 0, 0, 0};
     cudaStream_t capture_stream = nullptr;
 };
 
@@ -105,26 +108,30 @@ void free_ctx(bto_ctx *c) {
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     cudaFree(c->blocks);
     cudaFree(c->perm);
+    cudaFree(c->gblock);
     cudaFree(c->act[0]);
     cudaFree(c->act[1]);
+    cudaFree(c->gcnt[0]);
+    cudaFree(c->gcnt[1]);
     cudaFree(c->term);
-    cudaFree(c->cnt);
-    cudaFree(c->work);
+    cudaFree(c->diag_dst);
     delete c;
 }
 
-int chunk_size(const bto_ctx *c) { return c->nt * c->ppt; }
+int group_size(const bto_ctx *c) { return 32 * c->ppt; }
 
 bto_status configure_launch(bto_ctx *c) {
     const bool batched = c->nb > 1;
-    c->dyn_smem = batched ? (size_t)(c->nb + 1) * sizeof(int) : 0;
+    c->dyn_smem = 0;
     int occ = 0;
-    BTO_CUDA(bto::advect_occupancy(c->layout, c->nt, c->ppt, batched, c->dyn_smem, &occ));
+    BTO_CUDA(bto::advect_occupancy(c->layout, c->nt, c->ppt, c->cap, batched, c->dyn_smem, &occ));
     if (occ < 1) return BTO_ERR_UNSUPPORTED;
     const int per_sm = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, occ) : occ;
-    // Enough CTAs to fill every SM, never more than there are chunks.
-    const int64_t chunks = (c->P + chunk_size(c) - 1) / chunk_size(c);
-    c->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * per_sm, chunks));
+    // Enough CTAs to fill every SM, never more warps than there are groups.
+    const int64_t groups = c->slots / group_size(c);
+    const int64_t warps_per_cta = c->nt / 32;
+    const int64_t need = (groups + warps_per_cta - 1) / warps_per_cta;
+    c->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * per_sm, need));
     return BTO_OK;
 }
 
@@ -135,10 +142,13 @@ void drop_graph(bto_ctx *c) {
     }
 }
 
+int aux_grid(const bto_ctx *c) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((c->slots + 255) / 256, (int64_t)c->sm_count * 8));
+}
+
 bto_status seed(bto_ctx *c, cudaStream_t s) {
-    const int grid = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->sm_count * 8);
-    BTO_CUDA(bto::launch_seed(c->blocks, c->nb, c->perm, c->P, c->act[0], c->cnt, c->cnt + c->nb,
-                              c->work, std::max(grid, 1), s));
+    BTO_CUDA(bto::launch_seed(c->blocks, c->gblock, c->perm, c->slots, group_size(c), c->act[0],
+                              c->gcnt[0], aux_grid(c), s));
     c->cycle = 0;
     return BTO_OK;
 }
@@ -177,11 +187,22 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
         P += B.nseeds;
     }
     if (P > (1ll << 31) - 1) return BTO_ERR_INVALID_ARG;
+    int64_t slots = 0;
+    for (int32_t b = 0; b < nb; ++b) {
+        bl[(size_t)b].slot_base = slots;
+        slots += (bl[(size_t)b].nseeds + bto::kRegionAlign - 1) / bto::kRegionAlign * bto::kRegionAlign;
+    }
+    std::vector<int32_t> gblock((size_t)(slots / bto::kUnit));
+    for (int32_t b = 0; b < nb; ++b) {
+        const int64_t end = b + 1 < nb ? bl[(size_t)b + 1].slot_base : slots;
+        for (int64_t u = bl[(size_t)b].slot_base / bto::kUnit; u < end / bto::kUnit; ++u) gblock[(size_t)u] = b;
+    }
 
     bto_ctx *c = new (std::nothrow) bto_ctx();
     if (!c) return BTO_ERR_OOM;
     c->nb = nb;
     c->P = P;
+    c->slots = slots;
     c->L = L;
     c->blocks_h = bl;
     cudaError_t e = cudaGetDevice(&c->device);
@@ -191,21 +212,25 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     std::vector<int32_t> perm((size_t)P);
     for (int32_t b = 0; b < nb; ++b) morton_order(bl[(size_t)b].S, perm.data() + bl[(size_t)b].base);
 
+    const size_t units = (size_t)(slots / bto::kUnit);
     e = cudaMalloc(&c->blocks, sizeof(BlockDev) * (size_t)nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->act[0], sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->act[1], sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gblock, sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = cudaMalloc(&c->act[0], sizeof(float4) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->act[1], sizeof(float4) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[0], sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[1], sizeof(int32_t) * units);
     if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->cnt, sizeof(int32_t) * 3 * (size_t)nb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->work, sizeof(int32_t) * 3);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->blocks, bl.data(), sizeof(BlockDev) * (size_t)nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->perm, perm.data(), sizeof(int32_t) * (size_t)P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->gblock, gblock.data(), sizeof(int32_t) * units, cudaMemcpyHostToDevice);
     // term records start as "not terminated" (w = -1: all bits set)
     if (e == cudaSuccess) e = cudaMemset(c->term, 0xff, sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMemset(c->cnt, 0, sizeof(int32_t) * 3 * (size_t)nb);
-    if (e == cudaSuccess) e = cudaMemset(c->work, 0, sizeof(int32_t) * 3);
+    if (e == cudaSuccess) e = cudaMemset(c->gcnt[0], 0, sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = cudaMemset(c->gcnt[1], 0, sizeof(int32_t) * units);
     if (e != cudaSuccess) { (void)cudaGetLastError(); free_ctx(c); return cuda_status(e); }
 
     bto_status st = configure_launch(c);
@@ -223,20 +248,19 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     const int cyc = c->cycle;
     bto::AdvectArgs a;
     a.blocks = c->blocks;
+    a.gblock = c->gblock;
     a.nb = c->nb;
     a.cycle = cyc;
     a.field = field;
     a.fields = fields;
     a.in = c->act[cyc & 1];
     a.out = c->act[(cyc + 1) & 1];
-    a.cnt_in = c->cnt + (size_t)(cyc % 3) * c->nb;
-    a.cnt_out = c->cnt + (size_t)((cyc + 1) % 3) * c->nb;
-    a.cnt_zero = c->cnt + (size_t)((cyc + 2) % 3) * c->nb;
-    a.work = c->work + (cyc % 3);
-    a.work_zero = c->work + ((cyc + 1) % 3);
+    a.gcnt_in = c->gcnt[cyc & 1];
+    a.gcnt_out = c->gcnt[(cyc + 1) & 1];
+    a.ngroups = c->slots / group_size(c);
     a.term = c->term;
     a.dt = dt;
-    cudaError_t e = bto::launch_advect(a, c->layout, c->nt, c->ppt, c->grid, c->dyn_smem, s);
+    cudaError_t e = bto::launch_advect(a, c->layout, c->nt, c->ppt, c->cap, c->grid, c->dyn_smem, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         c->sticky = cuda_status(e);
@@ -307,7 +331,8 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
     if (ctx->cycle != 0) return BTO_ERR_STATE;
     const bool same = ctx->gexec && ctx->gtable == d_field_table && ctx->gdt == dt &&
                       ctx->gshape[0] == ctx->layout && ctx->gshape[1] == ctx->nt &&
-                      ctx->gshape[2] == ctx->ppt && ctx->gshape[3] == ctx->grid;
+                      ctx->gshape[2] == ctx->ppt && ctx->gshape[3] == ctx->grid &&
+                      ctx->gshape[4] == (ctx->cap ? 1 : 0);
     if (!same) {
         drop_graph(ctx);
         if (!ctx->capture_stream)
@@ -338,6 +363,7 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
         ctx->gshape[1] = ctx->nt;
         ctx->gshape[2] = ctx->ppt;
         ctx->gshape[3] = ctx->grid;
+        ctx->gshape[4] = ctx->cap ? 1 : 0;
     }
     BTO_CUDA(cudaGraphLaunch(ctx->gexec, (cudaStream_t)stream));
     ctx->cycle = ctx->L;
@@ -353,44 +379,52 @@ bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t
     if (ctx->cycle != ctx->L) return BTO_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int L = ctx->L;
-    const int grid = (int)std::max<int64_t>(
-        1, std::min<int64_t>((ctx->P + 255) / 256, (int64_t)ctx->sm_count * 8));
-    BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->nb, ctx->act[L & 1],
-                                    ctx->cnt + (size_t)(L % 3) * ctx->nb, ctx->P, d_ends, d_valid,
-                                    d_exit_cycle, grid, s));
+    const int grid = aux_grid(ctx);
+    BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, ctx->act[L & 1], ctx->gcnt[L & 1],
+                                    ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
+                                    grid, s));
     BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
                                     d_valid, d_exit_cycle, grid, s));
     return seed(ctx, s);
 }
 
 bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta, int32_t particles_per_thread,
-                          int32_t ctas_per_sm) {
+                          int32_t ctas_per_sm, int32_t reg_cap) {
     if (!ctx) return BTO_ERR_INVALID_ARG;
     if (threads_per_cta != 128 && threads_per_cta != 256) return BTO_ERR_INVALID_ARG;
     if (particles_per_thread != 1 && particles_per_thread != 2 && particles_per_thread != 4)
         return BTO_ERR_INVALID_ARG;
     if (ctas_per_sm < 0 || ctas_per_sm > 64) return BTO_ERR_INVALID_ARG;
+    if (reg_cap != 0 && reg_cap != 1) return BTO_ERR_INVALID_ARG;
     if (ctx->cycle != 0) return BTO_ERR_STATE;
-    const int o[3] = {ctx->nt, ctx->ppt, ctx->ctas_per_sm};
+    const int o[4] = {ctx->nt, ctx->ppt, ctx->ctas_per_sm, ctx->cap ? 1 : 0};
     ctx->nt = threads_per_cta;
     ctx->ppt = particles_per_thread;
     ctx->ctas_per_sm = ctas_per_sm;
+    ctx->cap = reg_cap != 0;
     bto_status st = configure_launch(ctx);
     if (st != BTO_OK) {
-        ctx->nt = o[0]; ctx->ppt = o[1]; ctx->ctas_per_sm = o[2];
+        ctx->nt = o[0]; ctx->ppt = o[1]; ctx->ctas_per_sm = o[2]; ctx->cap = o[3] != 0;
         configure_launch(ctx);
         return st;
     }
     drop_graph(ctx);
+    if (o[1] != ctx->ppt) {
+        // group counts depend on the group size: seed the interval afresh
+        BTO_CUDA(cudaDeviceSynchronize());
+        BTO_TRY(seed(ctx, 0));
+        BTO_CUDA(cudaDeviceSynchronize());
+    }
     return BTO_OK;
 }
 
-bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[4]) {
+bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]) {
     if (!ctx || !out) return BTO_ERR_INVALID_ARG;
     out[0] = ctx->nt;
     out[1] = ctx->ppt;
     out[2] = ctx->ctas_per_sm;
-    out[3] = ctx->grid;
+    out[3] = ctx->cap ? 1 : 0;
+    out[4] = ctx->grid;
     return BTO_OK;
 }
 
@@ -399,10 +433,29 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
     if (reinterpret_cast<uintptr_t>(d_out) % 16) return BTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int cyc = ctx->cycle;
-    BTO_CUDA(cudaMemcpyAsync(d_out, ctx->act[cyc & 1], sizeof(float4) * (size_t)ctx->P,
-                             cudaMemcpyDeviceToDevice, s));
-    BTO_CUDA(cudaMemcpyAsync(live, ctx->cnt + (size_t)(cyc % 3) * ctx->nb,
-                             sizeof(int32_t) * (size_t)ctx->nb, cudaMemcpyDeviceToHost, s));
+    const int G = group_size(ctx);
+    const int64_t ng = ctx->slots / G;
+    std::vector<int32_t> cnt((size_t)ng);
+    std::vector<int64_t> dst((size_t)ng);
+    BTO_CUDA(cudaMemcpyAsync(cnt.data(), ctx->gcnt[cyc & 1], sizeof(int32_t) * (size_t)ng,
+                             cudaMemcpyDeviceToHost, s));
+    BTO_CUDA(cudaStreamSynchronize(s));
+    for (int32_t b = 0; b < ctx->nb; ++b) {
+        const BlockDev &B = ctx->blocks_h[(size_t)b];
+        const int64_t g0 = B.slot_base / G;
+        const int64_t g1 = b + 1 < ctx->nb ? ctx->blocks_h[(size_t)b + 1].slot_base / G : ng;
+        int64_t run = B.base;
+        for (int64_t g = g0; g < g1; ++g) {
+            dst[(size_t)g] = run;
+            run += cnt[(size_t)g];
+        }
+        live[b] = (int32_t)(run - B.base);
+    }
+    if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)(ctx->slots / 32)));
+    BTO_CUDA(cudaMemcpyAsync(ctx->diag_dst, dst.data(), sizeof(int64_t) * (size_t)ng,
+                             cudaMemcpyHostToDevice, s));
+    BTO_CUDA(bto::launch_gather_live(ctx->act[cyc & 1], ctx->gcnt[cyc & 1], ctx->diag_dst, ctx->slots,
+                                     G, reinterpret_cast<float4 *>(d_out), aux_grid(ctx), s));
     BTO_CUDA(cudaStreamSynchronize(s));
     return BTO_OK;
 }

@@ -19,24 +19,32 @@ struct BlockDev {
     float origin[3];    // physical position of node (0,0,0)
     float h[3];         // spacing
     int32_t pad_;
-    int64_t base;       // first canonical id of the block == first slot of its list region
+    int64_t base;       // first canonical id of the block
+    int64_t slot_base;  // first slot of the block's list region (multiple of kRegionAlign)
     int64_t nseeds;     // seeds of the block
 };
 
+// Every block's list region starts at a multiple of kRegionAlign slots, so a
+// particle group (32 * particles-per-thread slots, a divisor of kRegionAlign)
+// never straddles two blocks. gblock[] maps each 32-slot unit to its block.
+constexpr int kRegionAlign = 128;
+constexpr int kUnit = 32;
+
 // Arguments of one advection cycle (kernel K3: RK4 + termination + compaction).
+// The active list is cut into groups of G = 32 * ppt slots; group g holds
+// gcnt[g] live particles in its first slots, in Morton order of their seeds.
 struct AdvectArgs {
     const BlockDev *blocks;      // [nb] device
+    const int32_t *gblock;       // [slots / 32] block of each 32-slot unit
     int32_t nb;
     int32_t cycle;               // cycle index within the interval
     const void *field;           // single field pointer (nb == 1 calls), or NULL
     const void *const *fields;   // device array [nb] used when field == NULL
     const float4 *in;            // active list at cycle start (xi, id bits)
     float4 *out;                 // active list after the cycle
-    const int32_t *cnt_in;       // [nb] live particles at cycle start
-    int32_t *cnt_out;            // [nb] survivors (zero on entry)
-    int32_t *cnt_zero;           // [nb] zeroed here: the next cycle's output counts
-    int32_t *work;               // chunk queue of this cycle (zero on entry)
-    int32_t *work_zero;          // zeroed here: the next cycle's chunk queue
+    const int32_t *gcnt_in;      // [ngroups] live particles per group at cycle start
+    int32_t *gcnt_out;           // [ngroups] survivors per group
+    int64_t ngroups;
     float4 *term;                // [P] termination record per canonical id
     float dt;
 };
@@ -44,16 +52,18 @@ struct AdvectArgs {
 enum { LAYOUT_F3 = 0, LAYOUT_F4 = 1 };
 
 // Kernel launchers (bto_kernels.cu). Each returns cudaGetLastError().
-cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, int grid,
+cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, bool cap, int grid,
                           size_t dyn_smem, cudaStream_t s);
-cudaError_t advect_occupancy(int layout, int nt, int ppt, bool batched, size_t dyn_smem,
+cudaError_t advect_occupancy(int layout, int nt, int ppt, bool cap, bool batched, size_t dyn_smem,
                              int *ctas_per_sm);
-cudaError_t launch_seed(const BlockDev *blocks, int32_t nb, const int32_t *perm, int64_t P,
-                        float4 *act, int32_t *cnt0, int32_t *cnt1, int32_t *work0,
-                        int grid, cudaStream_t s);
-cudaError_t launch_write_live(const BlockDev *blocks, int32_t nb, const float4 *act,
-                              const int32_t *cnt, int64_t P, float *ends, uint8_t *valid,
-                              int32_t *exit_cycle, int grid, cudaStream_t s);
+cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,
+                        int64_t slots, int group, float4 *act, int32_t *gcnt, int grid,
+                        cudaStream_t s);
+cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, const float4 *act,
+                              const int32_t *gcnt, int64_t slots, int group, float *ends,
+                              uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s);
+cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
+                               int64_t slots, int group, float4 *out, int grid, cudaStream_t s);
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,
                               float *seeds, float *ends, uint8_t *valid, int32_t *exit_cycle,
                               int grid, cudaStream_t s);

@@ -16,9 +16,9 @@
 // seeds so that neighbouring threads touch neighbouring cells (L1/L2 reuse
 // of each node); the 8 corners of a cell stay in registers across the four
 // RK4 stages and are reloaded only when a stage point lands in another cell;
-// survivors are compacted per chunk of NT*PPT particles with one atomic per
-// chunk; the grid is persistent (a multiple of the SM count) and takes
-// chunks from an atomic queue in list order.
+// each warp owns groups of 32*PPT particles and compacts the survivors of a
+// group inside that group (ballot/popc, no barrier, no atomic); the grid is
+// persistent (a multiple of the SM count).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -40,6 +40,10 @@ struct Cell {
     float v[8][3];  // corner (a, b, c) -> index a + 2b + 4c
 };
 
+// The 8 corner nodes of cell (ix, iy, iz), as four x-neighbour pairs. F4
+// nodes are one 16-byte load each; F3 nodes are three 4-byte loads each
+// (their 12-byte stride leaves no common alignment for wider loads; 16- and
+// 32-byte variants with in-register selection were measured slower).
 template <int LAYOUT>
 __device__ __forceinline__ void load_cell(const void *__restrict__ field, uint32_t nnx,
                                           uint32_t nnxy, int ix, int iy, int iz,
@@ -80,7 +84,7 @@ __device__ __forceinline__ float3 trilerp(const float (&v)[8][3], float fx, floa
     return make_float3(r[0], r[1], r[2]);
 }
 
-// Block geometry held in registers while a chunk is processed.
+// Block geometry held in registers while a group is processed.
 struct Geo {
     int nx, ny, nz;        // cells
     float fnx, fny, fnz;   // cells as float (closed-box test)
@@ -154,160 +158,90 @@ __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, i
 }
 
 // ---------------------------------------------------------------------------
-// K3: advection cycle. Persistent CTAs take chunks of CH = NT*PPT particles
-// of one block from an atomic queue; survivors of a chunk are written as one
-// contiguous run at a position reserved with one atomicAdd on the block's
-// output count (stable order inside the chunk).
+// K3: advection cycle. The active list is cut into groups of G = 32*PPT
+// slots; one warp owns a group for the cycle: it advects the group's live
+// particles (PPT rounds of 32) and writes the survivors, in order, to the
+// front of the same group in the output list. Warps take groups g, g + W,
+// g + 2W, ... (W = warps in the grid), so the groups in flight at any time
+// are neighbours in Morton order. There is no barrier and no atomic: a
+// terminated particle only leaves the group's live prefix.
 // ---------------------------------------------------------------------------
-template <int LAYOUT, int NT, int PPT, bool BATCHED>
-__global__ void __launch_bounds__(NT) advect_kernel(const AdvectArgs a) {
-    constexpr int NW = NT / 32;
-    constexpr int CH = NT * PPT;
-    static_assert(PPT * NW <= 32, "per-chunk warp counts must fit one warp scan");
-    __shared__ float4 s_buf[CH];
-    __shared__ int s_wcnt[PPT * NW];
-    __shared__ int s_wofs[PPT * NW];
-    __shared__ int s_g, s_base, s_total;
-    __shared__ int s_warp_sum[NW];
-    extern __shared__ int s_prefix[];  // BATCHED: nb + 1 chunk offsets
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    if (blockIdx.x == 0) {
-        for (int b = tid; b < a.nb; b += NT) a.cnt_zero[b] = 0;
-        if (tid == 0) *a.work_zero = 0;
-    }
-
-    int total;
-    if (BATCHED) {
-        // exclusive scan of per-block chunk counts into s_prefix[0..nb]
-        const int per = (a.nb + NT - 1) / NT;
-        const int b0 = tid * per, b1 = min(a.nb, b0 + per);
-        int local = 0;
-        for (int b = b0; b < b1; ++b) local += (__ldcg(a.cnt_in + b) + CH - 1) / CH;
-        int incl = local;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp_sum[warp] = incl;
-        __syncthreads();
-        int wofs = 0;
-        for (int w = 0; w < warp; ++w) wofs += s_warp_sum[w];
-        int run = wofs + incl - local;
-        for (int b = b0; b < b1; ++b) {
-            s_prefix[b] = run;
-            run += (__ldcg(a.cnt_in + b) + CH - 1) / CH;
-        }
-        if (tid == NT - 1) { s_prefix[a.nb] = wofs + incl; s_total = wofs + incl; }
-        __syncthreads();
-        total = s_total;
-    } else {
-        total = (__ldcg(a.cnt_in) + CH - 1) / CH;
-    }
-
+template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
+__global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
+    constexpr int G = 32 * PPT;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
     int cur_b = -1;
     Geo g{};
     float3 s = make_float3(0.f, 0.f, 0.f);
     const void *field = nullptr;
-    int64_t base = 0;
-    int Lb = 0;
+    int64_t idbase = 0;
 
-    for (;;) {
-        if (tid == 0) s_g = atomicAdd(a.work, 1);
-        __syncthreads();
-        const int gi = s_g;
-        if (gi >= total) break;
-        int b = 0, j = gi;
-        if (BATCHED) {
-            int lo = 0, hi = a.nb - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_prefix[mid] <= gi) lo = mid; else hi = mid - 1;
-            }
-            b = lo;
-            j = gi - s_prefix[b];
+    for (int64_t grp = (((int64_t)blockIdx.x * NT) + threadIdx.x) >> 5; grp < a.ngroups;
+         grp += nwarps) {
+        const int cnt = __ldcg(a.gcnt_in + grp);
+        if (cnt == 0) {
+            if (lane == 0) a.gcnt_out[grp] = 0;
+            continue;
         }
+        const int b = BATCHED ? __ldg(a.gblock + grp * PPT) : 0;
         if (b != cur_b) {
             cur_b = b;
             const BlockDev &B = a.blocks[b];
+            field = a.field ? a.field : a.fields[b];
             g = load_geo(B);
             s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
-            base = B.base;
-            field = a.field ? a.field : a.fields[b];
-            Lb = __ldcg(a.cnt_in + b);
+            idbase = B.base;
         }
-
-        unsigned mask = 0;
+        const int64_t s0 = grp * G;
+        float4 r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const int i = j * CH + k * NT + tid;
+            const int i = k * 32 + lane;
+            r[k] = i < cnt ? __ldcs(a.in + s0 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        int kept = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int i = k * 32 + lane;
             bool surv = false;
-            if (i < Lb) {
-                const float4 r = __ldcs(a.in + base + i);
-                float3 x = make_float3(r.x, r.y, r.z);
-                if (rk4_step<LAYOUT>(x, field, g, s)) {
-                    s_buf[k * NT + tid] = make_float4(x.x, x.y, x.z, r.w);
-                    surv = true;
+            if (i < cnt) {
+                float3 x = make_float3(r[k].x, r[k].y, r[k].z);
+                surv = rk4_step<LAYOUT>(x, field, g, s);
+                if (surv) {
+                    r[k].x = x.x; r[k].y = x.y; r[k].z = x.z;
                 } else {
-                    const int pid = __float_as_int(r.w);
-                    __stcs(a.term + base + pid, make_float4(r.x, r.y, r.z, __int_as_float(a.cycle)));
+                    __stcs(a.term + idbase + __float_as_int(r[k].w),
+                           make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
                 }
             }
-            const unsigned bal = __ballot_sync(kFull, surv);
-            if (lane == 0) s_wcnt[k * NW + warp] = __popc(bal);
-            mask |= (unsigned)surv << k;
+            const unsigned m = __ballot_sync(kFull, surv);
+            if (surv) __stcs(a.out + s0 + kept + __popc(m & lt), r[k]);
+            kept += __popc(m);
         }
-        __syncthreads();
-        if (warp == 0) {
-            const int v = lane < PPT * NW ? s_wcnt[lane] : 0;
-            int incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (lane < PPT * NW) s_wofs[lane] = incl - v;
-            const int tot = __shfl_sync(kFull, incl, 31);
-            if (lane == 0) s_base = tot ? atomicAdd(a.cnt_out + b, tot) : 0;
-        }
-        __syncthreads();
-        const int obase = s_base;
-        const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const bool surv = (mask >> k) & 1u;
-            const unsigned bal = __ballot_sync(kFull, surv);
-            if (surv) {
-                const int rank = s_wofs[k * NW + warp] + __popc(bal & lt);
-                __stcs(a.out + base + obase + rank, s_buf[k * NT + tid]);
-            }
-        }
-        __syncthreads();
+        if (lane == 0) a.gcnt_out[grp] = kept;
     }
 }
 
 // ---------------------------------------------------------------------------
-// K2: seeds. Slot i of block b holds lattice point perm[i] (Morton order of
-// the lattice); positions are exact integers j*s in cell units.
-// Also initialises the count ring for cycle 0.
+// K2: seeds. Slot i of block b's region holds the lattice point perm[base + m]
+// (m = i - slot_base; Morton order of the lattice); positions are the exact
+// integers j*s in cell units. Also sets every group's live count.
 // ---------------------------------------------------------------------------
-__global__ void seed_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
-                            const int32_t *__restrict__ perm, int64_t P, float4 *__restrict__ act,
-                            int32_t *cnt0, int32_t *cnt1, int32_t *work0) {
+__global__ void seed_kernel(const BlockDev *__restrict__ blocks, const int32_t *__restrict__ gblock,
+                            const int32_t *__restrict__ perm, int64_t slots, int group,
+                            float4 *__restrict__ act, int32_t *__restrict__ gcnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (blockIdx.x == 0) {
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            cnt0[b] = (int32_t)blocks[b].nseeds;
-            cnt1[b] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+        const BlockDev &B = blocks[gblock[i / kUnit]];
+        const int64_t m = i - B.slot_base;
+        if (i % group == 0) {
+            const int64_t left = B.nseeds - m;
+            gcnt[i / group] = (int32_t)(left < 0 ? 0 : (left > group ? group : left));
         }
-        if (threadIdx.x == 0) *work0 = 0;
-    }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
-        const int b = nb == 1 ? 0 : find_block(blocks, nb, i);
-        const BlockDev &B = blocks[b];
-        const int32_t p = perm[i];
+        if (m >= B.nseeds) continue;
+        const int32_t p = perm[B.base + m];
         const int32_t jx = p % B.S[0];
         const int32_t jy = (p / B.S[0]) % B.S[1];
         const int32_t jz = p / (B.S[0] * B.S[1]);
@@ -317,15 +251,15 @@ __global__ void seed_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
 }
 
 // K4a: particles alive at the end of the interval.
-__global__ void write_live_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
-                                  const float4 *__restrict__ act, const int32_t *__restrict__ cnt,
-                                  int64_t P, float *__restrict__ ends, uint8_t *__restrict__ valid,
-                                  int32_t *__restrict__ exit_cycle) {
+__global__ void write_live_kernel(const BlockDev *__restrict__ blocks,
+                                  const int32_t *__restrict__ gblock,
+                                  const float4 *__restrict__ act, const int32_t *__restrict__ gcnt,
+                                  int64_t slots, int group, float *__restrict__ ends,
+                                  uint8_t *__restrict__ valid, int32_t *__restrict__ exit_cycle) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
-        const int b = nb == 1 ? 0 : find_block(blocks, nb, i);
-        const BlockDev &B = blocks[b];
-        if (i - B.base >= (int64_t)cnt[b]) continue;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+        if (i % group >= gcnt[i / group]) continue;
+        const BlockDev &B = blocks[gblock[i / kUnit]];
         const float4 r = act[i];
         const int64_t gid = B.base + __float_as_int(r.w);
         ends[3 * gid + 0] = fmaf(r.x, B.h[0], B.origin[0]);
@@ -370,31 +304,45 @@ __global__ void write_term_kernel(const BlockDev *__restrict__ blocks, int32_t n
     }
 }
 
-template <int LAYOUT, int NT, int PPT, bool BATCHED>
+// Diagnostics: live particles of each group copied to dst[g] + k.
+__global__ void gather_live_kernel(const float4 *__restrict__ act, const int32_t *__restrict__ gcnt,
+                                   const int64_t *__restrict__ dst, int64_t slots, int group,
+                                   float4 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+        const int64_t g = i / group;
+        const int k = (int)(i % group);
+        if (k < gcnt[g]) out[dst[g] + k] = act[i];
+    }
+}
+
+template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 cudaError_t launch_t(const AdvectArgs &a, int grid, size_t dyn, cudaStream_t s) {
-    advect_kernel<LAYOUT, NT, PPT, BATCHED><<<grid, NT, dyn, s>>>(a);
+    advect_kernel<LAYOUT, NT, PPT, BATCHED, MINB><<<grid, NT, dyn, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int LAYOUT, int NT, int PPT, bool BATCHED>
+template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 cudaError_t occ_t(size_t dyn, int *n) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, advect_kernel<LAYOUT, NT, PPT, BATCHED>,
-                                                         NT, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        n, advect_kernel<LAYOUT, NT, PPT, BATCHED, MINB>, NT, dyn);
 }
 
-// Dispatch over the compiled launch shapes.
-#define BTO_SHAPES(X, L, B)                                                        \
-    X(L, 128, 1, B) X(L, 128, 2, B) X(L, 128, 4, B) X(L, 256, 1, B) X(L, 256, 2, B) \
-    X(L, 256, 4, B)
+// Dispatch over the compiled launch shapes: threads per CTA, particles per
+// thread, and whether registers are capped at 64 (1024 threads per SM).
+#define BTO_SHAPES(X, L, B)                                                                  \
+    X(L, 128, 1, B, 1) X(L, 128, 2, B, 1) X(L, 128, 4, B, 1) X(L, 256, 1, B, 1)                \
+    X(L, 256, 2, B, 1) X(L, 256, 4, B, 1) X(L, 128, 1, B, 8) X(L, 128, 2, B, 8)                \
+    X(L, 128, 4, B, 8) X(L, 256, 1, B, 4) X(L, 256, 2, B, 4) X(L, 256, 4, B, 4)
 
 }  // namespace
 
-cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, int grid,
+cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, bool cap, int grid,
                           size_t dyn, cudaStream_t s) {
     const bool batched = a.nb > 1;
-#define BTO_CASE(L, T, P, B)                                            \
-    if (layout == L && nt == T && ppt == P && batched == B)             \
-        return launch_t<L, T, P, B>(a, grid, dyn, s);
+#define BTO_CASE(L, T, P, B, M)                                                     \
+    if (layout == L && nt == T && ppt == P && batched == B && cap == (M > 1))       \
+        return launch_t<L, T, P, B, M>(a, grid, dyn, s);
     BTO_SHAPES(BTO_CASE, LAYOUT_F3, false)
     BTO_SHAPES(BTO_CASE, LAYOUT_F4, false)
     BTO_SHAPES(BTO_CASE, LAYOUT_F3, true)
@@ -403,9 +351,11 @@ cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, int 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t advect_occupancy(int layout, int nt, int ppt, bool batched, size_t dyn, int *n) {
-#define BTO_CASE(L, T, P, B)                                            \
-    if (layout == L && nt == T && ppt == P && batched == B) return occ_t<L, T, P, B>(dyn, n);
+cudaError_t advect_occupancy(int layout, int nt, int ppt, bool cap, bool batched, size_t dyn,
+                             int *n) {
+#define BTO_CASE(L, T, P, B, M)                                                     \
+    if (layout == L && nt == T && ppt == P && batched == B && cap == (M > 1))       \
+        return occ_t<L, T, P, B, M>(dyn, n);
     BTO_SHAPES(BTO_CASE, LAYOUT_F3, false)
     BTO_SHAPES(BTO_CASE, LAYOUT_F4, false)
     BTO_SHAPES(BTO_CASE, LAYOUT_F3, true)
@@ -414,17 +364,24 @@ cudaError_t advect_occupancy(int layout, int nt, int ppt, bool batched, size_t d
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_seed(const BlockDev *blocks, int32_t nb, const int32_t *perm, int64_t P,
-                        float4 *act, int32_t *cnt0, int32_t *cnt1, int32_t *work0, int grid,
+cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,
+                        int64_t slots, int group, float4 *act, int32_t *gcnt, int grid,
                         cudaStream_t s) {
-    seed_kernel<<<grid, 256, 0, s>>>(blocks, nb, perm, P, act, cnt0, cnt1, work0);
+    seed_kernel<<<grid, 256, 0, s>>>(blocks, gblock, perm, slots, group, act, gcnt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_write_live(const BlockDev *blocks, int32_t nb, const float4 *act,
-                              const int32_t *cnt, int64_t P, float *ends, uint8_t *valid,
-                              int32_t *exit_cycle, int grid, cudaStream_t s) {
-    write_live_kernel<<<grid, 256, 0, s>>>(blocks, nb, act, cnt, P, ends, valid, exit_cycle);
+cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, const float4 *act,
+                              const int32_t *gcnt, int64_t slots, int group, float *ends,
+                              uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s) {
+    write_live_kernel<<<grid, 256, 0, s>>>(blocks, gblock, act, gcnt, slots, group, ends, valid,
+                                           exit_cycle);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
+                               int64_t slots, int group, float4 *out, int grid, cudaStream_t s) {
+    gather_live_kernel<<<grid, 256, 0, s>>>(act, gcnt, dst, slots, group, out);
     return cudaGetLastError();
 }
 
