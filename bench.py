@@ -89,24 +89,32 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def max_over_ranks(v, world, device="cuda"):
     if world <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def sum_over_ranks(v, world):
+def sum_over_ranks(v, world, device="cuda"):
     if world <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def aggregate(units, seconds, world, device="cuda"):
+    """Whole-job throughput: units of all ranks over the slowest rank's time.
+    Host-side reporting only; the per-cycle path has no collective."""
+    total = sum_over_ranks(float(units), world, device)
+    slowest = max_over_ranks(float(seconds), world, device)
+    return total, slowest, total / slowest
 
 
 # ---------------------------------------------------------------------------
@@ -178,14 +186,18 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def block_layout():
+def block_layout(rank=0, world=1):
+    """Blocks of one rank. The job's domain is (2*world) x 2 x 2 blocks of
+    128^3 cells (each rank's 2x2x2 share is a 256^3-cell cube); rank r owns
+    the blocks with bx in {2r, 2r+1}. Weak scaling: every rank has the same
+    work, and the blocks of different ranks never overlap."""
     nbx = GLOBAL_CELLS // BLOCK_CELLS
     h = 1.0 / GLOBAL_CELLS
     blocks = []
     for bz in range(nbx):
         for by in range(nbx):
             for bx in range(nbx):
-                blocks.append((bx, by, bz))
+                blocks.append((bx + nbx * rank, by, bz))
     ext = [(BLOCK_CELLS,) * 3] * len(blocks)
     org = [(b[0] * BLOCK_CELLS * h, b[1] * BLOCK_CELLS * h, b[2] * BLOCK_CELLS * h) for b in blocks]
     spc = [(h, h, h)] * len(blocks)
@@ -193,17 +205,22 @@ def block_layout():
 
 
 def synth_fields(modes, blocks, cycles, device, with_global=False):
-    """Per-cycle block fields (F3, contiguous) generated in device memory."""
+    """Per-cycle block fields (F3, contiguous) generated in device memory: the
+    rank's 256^3-cell cube is synthesised whole (257^3 nodes) and cut into its
+    8 blocks with shared faces."""
     import torch
     from paper_2004_02003_gb300 import inputs
     G = GLOBAL_CELLS
     h = 1.0 / G
     n = BLOCK_CELLS
+    bx0 = min(b[0] for b in blocks)
+    x0 = bx0 * n * h
     per_cycle, glob = [], []
     for c in range(cycles):
-        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), c, device)
+        gf = inputs.fourier_field_torch(modes, (G, G, G), (x0, 0, 0), (h, h, h), c, device)
         row = []
         for (bx, by, bz) in blocks:
+            bx -= bx0
             row.append(gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous())
         per_cycle.append(row)
         if with_global:
@@ -260,6 +277,19 @@ def algorithmic_bytes(live, nodes_touched, L):
     return 12 * nodes_touched + 24 * live + 17 * term
 
 
+def measured_traffic():
+    """DRAM bytes (read + write) of one advect launch from the committed ncu
+    capture, or None when the kernel source has changed since the capture."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "advect_turb256_traffic.json")
+    src = os.path.join(ROOT, "paper_2004_02003_gb300", "csrc", "bto_kernels.cu")
+    if not os.path.exists(rec):
+        return None
+    d = json.load(open(rec))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d["dram_bytes_per_launch"] if sha.startswith(d["kernel_source_sha256_prefix"]) else None
+
+
 def run_ours(args):
     import torch
     from paper_2004_02003_gb300 import bto, inputs
@@ -274,7 +304,7 @@ def run_ours(args):
     modes = inputs.fourier_modes(SEED, m=NMODES, kmin=1.0, kmax=16.0, drift_max=0.05)
     h = 1.0 / GLOBAL_CELLS
     dt = 0.25 * h  # max|u| = 1 after normalisation -> 0.25 cells per step at max speed
-    blocks, ext, org, spc = block_layout()
+    blocks, ext, org, spc = block_layout(rank, world)
     nb = len(blocks)
     L = INTERVAL
     nf = max(1, min(args.fields, L))
@@ -346,9 +376,7 @@ def run_ours(args):
     # every step computes the same interval: check it reproduced the units
     assert np.array_equal(out["exit_cycle"].cpu().numpy(), exit_np), "steps differ"
 
-    elapsed_max = max_over_ranks(elapsed, world)
-    total_psteps = sum_over_ranks(float(psteps * args.steps), world)
-    value = total_psteps / elapsed_max
+    total_psteps, elapsed_max, value = aggregate(psteps * args.steps, elapsed, world)
     advect_s = sum(launch_ms) / 1e3
 
     # roofline of the advection kernel (dominant): algorithmic bytes of each
@@ -362,6 +390,7 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     algo = algorithmic_bytes(live, nodes_touched, L)
+    traffic = measured_traffic()
     achieved = float(algo.sum()) / advect_s / 1e9
     frac = achieved / peak
 
@@ -393,7 +422,7 @@ def run_ours(args):
         "terminated_frac": float(1.0 - valid_np.mean()),
         "gpu_launches": args.steps * (L + 3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": frac,
-                     "traffic": None, "peak_source": peak_src,
+                     "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": float(algo.mean()),
                      "avg_launch_ms": float(np.mean(launch_ms)),
                      "launch_ms_by_decile": [round(float(np.mean(launch_ms[k:k + L // 10])), 4)

@@ -1,0 +1,68 @@
+"""Multi-rank host logic of the benchmark on CPU (gloo, world size 2).
+
+BTO needs no communication during an interval (each block is advanced
+independently, Sec. 3.1), so the multi-GPU path shards whole blocks across
+ranks and only the host-side reporting reduces two numbers at the end. These
+tests run that logic with the gloo backend in two spawned processes.
+"""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                      RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        blocks, ext, org, spc = bench.block_layout(rank, world)
+        total, slowest, value = bench.aggregate(1000 * (rank + 1), 0.5 * (rank + 1), world, device="cpu")
+        q.put((rank, blocks, org, total, slowest, value))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_shard_blocks_and_aggregate():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        results = sorted([q.get(timeout=120) for _ in range(2)])
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    assert all(p.exitcode == 0 for p in procs)
+    blocks = [set(r[1]) for r in results]
+    assert not (blocks[0] & blocks[1])                       # disjoint
+    union = blocks[0] | blocks[1]
+    assert union == {(bx, by, bz) for bx in range(4) for by in range(2) for bz in range(2)}
+    for r in results:
+        assert len(r[1]) == 8                                 # same work per rank (weak)
+        assert r[3] == 3000.0 and r[4] == 1.0 and r[5] == 3000.0
+    # origins follow the block indices at 128 cells of 1/256
+    for (bx, by, bz), o in zip(results[1][1], results[1][2]):
+        assert o == (bx * 0.5, by * 0.5, bz * 0.5)
+
+
+def test_single_rank_layout_is_the_256_cube():
+    import bench
+    blocks, ext, org, spc = bench.block_layout(0, 1)
+    assert sorted(blocks) == sorted((bx, by, bz) for bx in range(2) for by in range(2) for bz in range(2))
+    assert bench.aggregate(10, 2.0, 1) == (10, 2.0, 5.0)
