@@ -190,6 +190,46 @@ BTO_API bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live,
  * work; clears the sticky state. */
 BTO_API bto_status bto_last_error(bto_ctx *ctx);
 
+/* ---- Allocation-free interval (no counterpart in the paper) -------------
+ *
+ * For callers that cannot let a library allocate device memory: for example an
+ * in situ simulation that gives all device memory to its own pool allocator at
+ * start-up and forbids allocations by analysis libraries while it runs, which
+ * rules out bto_create (it allocates the particle state). This call runs one
+ * whole interval of one block (seed, interval_cycles RK4 cycles with
+ * termination, basis-flow output: the same kernels as the context calls)
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The particle state lives in a fixed array of BTO_NOALLOC_SCRATCH_BYTES in
+ * the library's device image. Every device that loads the library holds that
+ * array until the process exits. All calls on a device share it, and it keeps
+ * the last call's contents (each call rewrites what it reads first), so calls
+ * whose GPU work overlaps (different streams, or several host threads) race
+ * with each other and give wrong results: order them on one stream.
+ * The first call on each device, made with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and keeps it; make that first
+ * call before any stream capture.
+ *
+ *   extent_cells, origin, spacing, seed_stride, interval_cycles
+ *                  as in bto_create; at most BTO_NOALLOC_MAX_SEEDS seeds
+ *                  (more returns BTO_ERR_UNSUPPORTED, nothing launched)
+ *   d_field_table  DEVICE array of interval_cycles device pointers: entry c
+ *                  is the F3_AOS field of cycle c
+ *   dt             step of every cycle (finite)
+ *   d_seeds, d_ends, d_valid, d_exit_cycle
+ *                  outputs as in bto_end_interval (d_exit_cycle may be NULL)
+ *   stream         all work is enqueued on it; the call does not wait
+ * Seeds are processed in canonical lattice order (not Morton order); the
+ * outputs are identical to the context calls'. */
+#define BTO_NOALLOC_MAX_SEEDS 65536
+#define BTO_NOALLOC_SCRATCH_BYTES 3432704
+BTO_API bto_status bto_interval_noalloc(const int32_t extent_cells[3], const float origin[3],
+                                        const float spacing[3], int32_t seed_stride,
+                                        int32_t interval_cycles,
+                                        const void *const *d_field_table, float dt,
+                                        float *d_seeds, float *d_ends, uint8_t *d_valid,
+                                        int32_t *d_exit_cycle, bto_stream stream);
+
 /* Static string for a status code. */
 BTO_API const char *bto_status_string(bto_status status);
 

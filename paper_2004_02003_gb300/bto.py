@@ -60,6 +60,8 @@ def _declare(lib):
         "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
         "bto_last_error": ([vp], ctypes.c_int),
         "bto_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "bto_interval_noalloc": ([c_i32p, c_fp, c_fp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_float,
+                                  vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -200,6 +202,18 @@ def bto_copy_active(ctx: int, d_out, stream=None) -> list:
 
 def bto_last_error(ctx: int) -> int:
     return int(load().bto_last_error(ctx))
+
+
+def bto_interval_noalloc(extent_cells, origin, spacing, seed_stride: int, interval_cycles: int,
+                         d_field_table, dt: float, d_seeds, d_ends, d_valid, d_exit_cycle=None,
+                         stream=None) -> None:
+    """One whole interval of one block with no device allocation by the
+    library (state in a static device array; see include/bto.h)."""
+    _check(load().bto_interval_noalloc(_arr(ctypes.c_int32, extent_cells), _arr(ctypes.c_float, origin),
+                                       _arr(ctypes.c_float, spacing), int(seed_stride), int(interval_cycles),
+                                       _addr(d_field_table), float(dt), _addr(d_seeds), _addr(d_ends),
+                                       _addr(d_valid), _addr(d_exit_cycle), _stream(stream)),
+           "bto_interval_noalloc")
 
 
 def bto_status_string(status: int) -> str:
