@@ -72,6 +72,10 @@ def _load():
     lib.bto_oracle_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int32,
                                      ctypes.c_int64, dp, i32p, dp, ctypes.c_int32]
     lib.bto_oracle_cycle.restype = None
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.bto_oracle_adjoint_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int64, dp, u8p, dp,
+                                             dp, ctypes.c_int32]
+    lib.bto_oracle_adjoint_cycle.restype = None
     lib.bto_oracle_max_threads.argtypes = []
     lib.bto_oracle_max_threads.restype = ctypes.c_int32
     _lib = lib
@@ -202,6 +206,61 @@ def run_interval(grid: Grid, stride: int, cycles: int, dt: float, field_of_cycle
     for c in range(cycles):
         cycle(grid, field_of_cycle(c0 + c), dt, c, st, nthreads)
     return st
+
+
+# ---------------------------------------------------------------------------
+# Discrete adjoint (gradients of a loss on end positions)
+# ---------------------------------------------------------------------------
+def adjoint_cycle(grid: Grid, field: np.ndarray, dt: float, x: np.ndarray, alive: np.ndarray,
+                  lam: np.ndarray, grad_field=None, nthreads: int = 0) -> None:
+    """Reverse of one cycle: lam (m, 3) holds dL/dx after the cycle on entry
+    and dL/dx before it on return, for particles whose step was taken
+    (alive = 1). grad_field, if given, is a float64 array shaped like the
+    field and is accumulated."""
+    lib = _load()
+    field = _check_field(grid, field)
+    n, o, h = grid._arrays()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    alive = np.ascontiguousarray(alive, dtype=np.uint8)
+    assert lam.dtype == np.float64 and lam.flags.c_contiguous
+    gp = None
+    if grad_field is not None:
+        assert grad_field.dtype == np.float64 and grad_field.flags.c_contiguous
+        assert grad_field.size == field.size
+        gp = _ptr(grad_field, ctypes.c_double)
+    lib.bto_oracle_adjoint_cycle(_ptr(field, ctypes.c_float), _ptr(n, ctypes.c_int64),
+                                 _ptr(o, ctypes.c_double), _ptr(h, ctypes.c_double), float(dt),
+                                 x.shape[0], _ptr(x, ctypes.c_double), _ptr(alive, ctypes.c_uint8),
+                                 _ptr(lam, ctypes.c_double), gp, int(nthreads))
+
+
+def forward_with_history(grid: Grid, field_of_cycle, dt: float, x0: np.ndarray, cycles: int):
+    """Forward from arbitrary start positions, keeping every cycle's
+    positions: returns (state, xs) with xs[c] the positions at the start of
+    cycle c (xs[cycles] = end positions)."""
+    st = State(x0)
+    xs = [st.x.copy()]
+    for c in range(cycles):
+        cycle(grid, field_of_cycle(c), dt, c, st)
+        xs.append(st.x.copy())
+    return st, xs
+
+
+def vjp(grid: Grid, field_of_cycle, dt: float, x0: np.ndarray, cycles: int, grad_end: np.ndarray,
+        want_field_grads: bool = False):
+    """Gradient of <grad_end, x_end(x0, F)> with respect to x0 (and, if asked,
+    to every cycle's node velocities), by the discrete adjoint. A terminated
+    particle's end is its last in-block position, reached by the steps
+    before its exit cycle."""
+    st, xs = forward_with_history(grid, field_of_cycle, dt, x0, cycles)
+    lam = np.ascontiguousarray(grad_end, dtype=np.float64).reshape(-1, 3).copy()
+    gF = [None] * cycles
+    for c in reversed(range(cycles)):
+        alive = ((st.exit_cycle < 0) | (st.exit_cycle > c)).astype(np.uint8)
+        g = np.zeros(grid.node_shape, dtype=np.float64) if want_field_grads else None
+        adjoint_cycle(grid, field_of_cycle(c), dt, xs[c], alive, lam, g)
+        gF[c] = g
+    return st, lam, gF
 
 
 # ---------------------------------------------------------------------------

@@ -209,6 +209,136 @@ ORACLE_API void bto_oracle_cycle(const float *field, const int64_t n[3],
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint of one cycle (reverse mode through the steps of
+ * bto_oracle_cycle), for the gradient of a loss on end positions with
+ * respect to seeds and node velocities. Termination is a discrete decision:
+ * a particle whose step of this cycle was taken (alive[p] = 1) passes its
+ * gradient back through that step; the others are left unchanged.
+ *
+ * Velocity and its derivative at q: with t = (q - origin)/h - i per axis,
+ * v = sum_corners w(t) F_corner and dv/dq_b = sum_corners (dw/dt_b) F / h_b,
+ * where w = w_a(tx) w_b(ty) w_c(tz) (Eq. 1 per axis) and dw_a/dt = +1 for
+ * the upper corner, -1 for the lower.
+ *
+ * Reverse of  x' = x + dt/6 (k1 + 2 k2 + 2 k3 + k4),
+ *             k1 = v(x), k2 = v(x + dt/2 k1), k3 = v(x + dt/2 k2),
+ *             k4 = v(x + dt k3),
+ * given lam = dL/dx':  g1 = dt/6 lam, g2 = g3 = dt/3 lam, g4 = dt/6 lam,
+ * then for stage 4, 3, 2: qbar = (dv/dq)^T g_s; lam_x += qbar; the stage
+ * before receives (dt or dt/2) qbar; stage 1 adds (dv/dx)^T g1 to lam_x.
+ * Each stage also adds w(q) g_s to the gradient of its 8 corner nodes.
+ *   x      m*3 positions at the START of the cycle
+ *   alive  m flags: 1 = the step of this cycle was taken
+ *   lam    m*3, in: dL/dx after the cycle, out: dL/dx before it
+ *   gF     NULL or nodes*3 doubles, accumulated (+=)
+ * ------------------------------------------------------------------------- */
+static void sample_jac(const float *field, const int64_t n[3], const double origin[3],
+                       const double h[3], const double q[3], double v[3], double J[3][3],
+                       size_t nodes_out[8], double w_out[8])
+{
+    int64_t cell[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+        double xi = (q[a] - origin[a]) / h[a];
+        int64_t i = (int64_t)floor(xi);
+        if (i < 0) i = 0;
+        if (i > n[a] - 1) i = n[a] - 1;
+        cell[a] = i;
+        t[a] = xi - (double)i;
+    }
+    const int64_t nx = n[0] + 1, ny = n[1] + 1;
+    for (int a = 0; a < 3; ++a) {
+        v[a] = 0.0;
+        J[a][0] = J[a][1] = J[a][2] = 0.0;
+    }
+    int k = 0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a, ++k) {
+                double wx = a ? t[0] : 1.0 - t[0], dwx = a ? 1.0 : -1.0;
+                double wy = b ? t[1] : 1.0 - t[1], dwy = b ? 1.0 : -1.0;
+                double wz = c ? t[2] : 1.0 - t[2], dwz = c ? 1.0 : -1.0;
+                double w = wx * wy * wz;
+                double dw[3] = {dwx * wy * wz / h[0], wx * dwy * wz / h[1], wx * wy * dwz / h[2]};
+                size_t node = (size_t)(cell[0] + a) +
+                              (size_t)nx * ((size_t)(cell[1] + b) + (size_t)ny * (size_t)(cell[2] + c));
+                const float *f = field + 3 * node;
+                for (int comp = 0; comp < 3; ++comp) {
+                    v[comp] += w * (double)f[comp];
+                    for (int d = 0; d < 3; ++d) J[comp][d] += dw[d] * (double)f[comp];
+                }
+                nodes_out[k] = node;
+                w_out[k] = w;
+            }
+}
+
+static void scatter(double *gF, const size_t nodes[8], const double w[8], const double g[3])
+{
+    if (!gF) return;
+    for (int k = 0; k < 8; ++k)
+        for (int comp = 0; comp < 3; ++comp) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+            gF[3 * nodes[k] + comp] += w[k] * g[comp];
+        }
+}
+
+ORACLE_API void bto_oracle_adjoint_cycle(const float *field, const int64_t n[3],
+                                         const double origin[3], const double h[3],
+                                         double dt, int64_t m, const double *x,
+                                         const uint8_t *alive, double *lam, double *gF,
+                                         int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t p = 0; p < m; ++p) {
+        if (!alive[p]) continue;
+        const double *xp = x + 3 * p;
+        double k1[3], k2[3], k3[3], k4[3], q2[3], q3[3], q4[3];
+        double J1[3][3], J2[3][3], J3[3][3], J4[3][3];
+        size_t n1[8], n2[8], n3[8], n4[8];
+        double w1[8], w2[8], w3[8], w4[8];
+        /* forward stages (same steps as bto_oracle_cycle) */
+        sample_jac(field, n, origin, h, xp, k1, J1, n1, w1);
+        for (int a = 0; a < 3; ++a) q2[a] = xp[a] + 0.5 * dt * k1[a];
+        sample_jac(field, n, origin, h, q2, k2, J2, n2, w2);
+        for (int a = 0; a < 3; ++a) q3[a] = xp[a] + 0.5 * dt * k2[a];
+        sample_jac(field, n, origin, h, q3, k3, J3, n3, w3);
+        for (int a = 0; a < 3; ++a) q4[a] = xp[a] + dt * k3[a];
+        sample_jac(field, n, origin, h, q4, k4, J4, n4, w4);
+        /* reverse */
+        double *lp = lam + 3 * p;
+        double g1[3], g2[3], g3[3], g4[3], lx[3], qb[3];
+        for (int a = 0; a < 3; ++a) {
+            g1[a] = dt / 6.0 * lp[a];
+            g2[a] = dt / 3.0 * lp[a];
+            g3[a] = dt / 3.0 * lp[a];
+            g4[a] = dt / 6.0 * lp[a];
+            lx[a] = lp[a];
+        }
+        /* stage 4: k4 = v(q4), q4 = x + dt k3 */
+        for (int d = 0; d < 3; ++d) qb[d] = J4[0][d] * g4[0] + J4[1][d] * g4[1] + J4[2][d] * g4[2];
+        scatter(gF, n4, w4, g4);
+        for (int a = 0; a < 3; ++a) { lx[a] += qb[a]; g3[a] += dt * qb[a]; }
+        /* stage 3: k3 = v(q3), q3 = x + dt/2 k2 */
+        for (int d = 0; d < 3; ++d) qb[d] = J3[0][d] * g3[0] + J3[1][d] * g3[1] + J3[2][d] * g3[2];
+        scatter(gF, n3, w3, g3);
+        for (int a = 0; a < 3; ++a) { lx[a] += qb[a]; g2[a] += 0.5 * dt * qb[a]; }
+        /* stage 2: k2 = v(q2), q2 = x + dt/2 k1 */
+        for (int d = 0; d < 3; ++d) qb[d] = J2[0][d] * g2[0] + J2[1][d] * g2[1] + J2[2][d] * g2[2];
+        scatter(gF, n2, w2, g2);
+        for (int a = 0; a < 3; ++a) { lx[a] += qb[a]; g1[a] += 0.5 * dt * qb[a]; }
+        /* stage 1: k1 = v(x) */
+        for (int d = 0; d < 3; ++d) qb[d] = J1[0][d] * g1[0] + J1[1][d] * g1[1] + J1[2][d] * g1[2];
+        scatter(gF, n1, w1, g1);
+        for (int a = 0; a < 3; ++a) lp[a] = lx[a] + qb[a];
+    }
+}
+
 ORACLE_API int32_t bto_oracle_max_threads(void)
 {
 #ifdef _OPENMP
