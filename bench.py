@@ -277,17 +277,24 @@ def algorithmic_bytes(live, nodes_touched, L):
     return 12 * nodes_touched + 24 * live + 17 * term
 
 
+def kernel_source_sha256():
+    """Hash of the advection kernel's sources (kernel file + shared device
+    functions): ties a recorded ncu capture to the code it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("bto_kernels.cu", "bto_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2004_02003_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic():
     """DRAM bytes (read + write) of one advect launch from the committed ncu
     capture, or None when the kernel source has changed since the capture."""
-    import hashlib
     rec = os.path.join(ROOT, "profiles", "advect_turb256_traffic.json")
-    src = os.path.join(ROOT, "paper_2004_02003_gb300", "csrc", "bto_kernels.cu")
     if not os.path.exists(rec):
         return None
     d = json.load(open(rec))
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return d["dram_bytes_per_launch"] if sha.startswith(d["kernel_source_sha256_prefix"]) else None
+    return d["dram_bytes_per_launch"] if kernel_source_sha256().startswith(d["kernel_source_sha256_prefix"]) else None
 
 
 def run_ours(args):

@@ -190,6 +190,65 @@ BTO_API bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live,
  * work; clears the sticky state. */
 BTO_API bto_status bto_last_error(bto_ctx *ctx);
 
+/* ---- Adjoint: gradients of a loss on end positions ----------------------
+ *
+ * The basis flow of a particle is a function of its start position and of
+ * every cycle's node velocities (Sec. 3.1 advection, Eq. 1 sampling). A tape
+ * runs one interval of one block from caller-given start positions, keeps
+ * positions every checkpoint_every cycles, and then returns vector-Jacobian
+ * products of the end positions: with respect to the start positions (the
+ * flow-map Jacobian, from which FTLE) and to the node velocities. Segments
+ * between checkpoints are recomputed during the backward sweep.
+ * A terminated particle's end is its last in-block position; its gradient
+ * flows back through the cycles before its exit cycle only (termination
+ * itself is a discrete decision with no gradient). Particles occupy fixed
+ * slots (no compaction); start positions outside the block never move.
+ * Only the F3_AOS field layout is accepted. */
+typedef struct bto_tape bto_tape;
+
+/* extent_cells, origin, spacing as in bto_create; num_particles >= 1;
+ * cycles >= 1; checkpoint_every >= 1 (clamped to cycles). Allocates
+ * (cycles/checkpoint_every + 2 + checkpoint_every) * num_particles * 16 B. */
+BTO_API bto_status bto_tape_create(const int32_t extent_cells[3], const float origin[3],
+                                   const float spacing[3], int64_t num_particles,
+                                   int32_t cycles, int32_t checkpoint_every, bto_tape **out);
+
+/* Particles of the tape, or -1 for NULL. */
+BTO_API int64_t bto_tape_num_particles(const bto_tape *tape);
+
+/* Forward interval.
+ *   d_seeds        P*3 floats, start positions (physical)
+ *   d_field_table  DEVICE array of `cycles` device pointers (F3_AOS fields);
+ *                  the table and the fields must stay valid until the last
+ *                  backward/jacobian call of this forward has completed
+ *   d_ends, d_valid, d_exit_cycle (nullable): as in bto_end_interval */
+BTO_API bto_status bto_tape_forward(bto_tape *tape, const float *d_seeds,
+                                    const void *const *d_field_table, float dt, float *d_ends,
+                                    uint8_t *d_valid, int32_t *d_exit_cycle, bto_stream stream);
+
+/* Reverse sweep of the last forward.
+ *   d_grad_ends          P*3 floats: dL/d(end position)
+ *   d_grad_seeds         P*3 floats written: dL/d(start position)
+ *   d_grad_field_table   NULL, or DEVICE array of `cycles` device pointers to
+ *                        F3-shaped float buffers that receive (+=) dL/d(node
+ *                        velocity) of each cycle (scatter-add with atomics)
+ * BTO_ERR_STATE without a forward. */
+BTO_API bto_status bto_tape_backward(bto_tape *tape, const float *d_grad_ends,
+                                     float *d_grad_seeds, float *const *d_grad_field_table,
+                                     bto_stream stream);
+
+/* Flow-map Jacobian of the last forward: d_jac (P*9 floats, row-major per
+ * particle) receives J[a][b] = d end_a / d start_b (three reverse sweeps). */
+BTO_API bto_status bto_tape_jacobian(bto_tape *tape, float *d_jac, bto_stream stream);
+
+/* FTLE from a Jacobian: d_ftle[p] = ln(sqrt(lambda_max(J^T J))) / |cycles*dt|
+ * for particles valid over the interval, NaN for terminated ones. */
+BTO_API bto_status bto_tape_ftle(bto_tape *tape, const float *d_jac, float *d_ftle,
+                                 bto_stream stream);
+
+/* Wait for outstanding work, then free the tape. NULL is a no-op. */
+BTO_API void bto_tape_destroy(bto_tape *tape);
+
 /* ---- Allocation-free interval (no counterpart in the paper) -------------
  *
  * For callers that cannot let a library allocate device memory: for example an

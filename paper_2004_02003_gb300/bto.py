@@ -63,6 +63,14 @@ def _declare(lib):
         "bto_interval_noalloc": ([c_i32p, c_fp, c_fp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_float,
                                   vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_destroy": ([vp], None),
+        "bto_tape_create": ([c_i32p, c_fp, c_fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                             ctypes.POINTER(vp)], ctypes.c_int),
+        "bto_tape_num_particles": ([vp], ctypes.c_int64),
+        "bto_tape_forward": ([vp, vp, vp, ctypes.c_float, vp, vp, vp, vp], ctypes.c_int),
+        "bto_tape_backward": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "bto_tape_jacobian": ([vp, vp, vp], ctypes.c_int),
+        "bto_tape_ftle": ([vp, vp, vp, vp], ctypes.c_int),
+        "bto_tape_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +222,43 @@ def bto_interval_noalloc(extent_cells, origin, spacing, seed_stride: int, interv
                                        _addr(d_field_table), float(dt), _addr(d_seeds), _addr(d_ends),
                                        _addr(d_valid), _addr(d_exit_cycle), _stream(stream)),
            "bto_interval_noalloc")
+
+
+def bto_tape_create(extent_cells, origin, spacing, num_particles: int, cycles: int,
+                    checkpoint_every: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().bto_tape_create(_arr(ctypes.c_int32, extent_cells), _arr(ctypes.c_float, origin),
+                                  _arr(ctypes.c_float, spacing), int(num_particles), int(cycles),
+                                  int(checkpoint_every), ctypes.byref(out)), "bto_tape_create")
+    return out.value
+
+
+def bto_tape_num_particles(tape: int) -> int:
+    return int(load().bto_tape_num_particles(tape))
+
+
+def bto_tape_forward(tape: int, d_seeds, d_field_table, dt: float, d_ends, d_valid, d_exit_cycle=None,
+                     stream=None) -> None:
+    _check(load().bto_tape_forward(tape, _addr(d_seeds), _addr(d_field_table), float(dt), _addr(d_ends),
+                                   _addr(d_valid), _addr(d_exit_cycle), _stream(stream)), "bto_tape_forward")
+
+
+def bto_tape_backward(tape: int, d_grad_ends, d_grad_seeds, d_grad_field_table=None, stream=None) -> None:
+    _check(load().bto_tape_backward(tape, _addr(d_grad_ends), _addr(d_grad_seeds), _addr(d_grad_field_table),
+                                    _stream(stream)), "bto_tape_backward")
+
+
+def bto_tape_jacobian(tape: int, d_jac, stream=None) -> None:
+    _check(load().bto_tape_jacobian(tape, _addr(d_jac), _stream(stream)), "bto_tape_jacobian")
+
+
+def bto_tape_ftle(tape: int, d_jac, d_ftle, stream=None) -> None:
+    _check(load().bto_tape_ftle(tape, _addr(d_jac), _addr(d_ftle), _stream(stream)), "bto_tape_ftle")
+
+
+def bto_tape_destroy(tape: int) -> None:
+    if tape:
+        load().bto_tape_destroy(tape)
 
 
 def bto_status_string(status: int) -> str:

@@ -23,129 +23,14 @@
 #include <cuda_runtime.h>
 
 #include "bto_internal.h"
+#include "bto_device.cuh"
 
 namespace bto {
 namespace {
 
+using namespace dev;
+
 constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------------------
-// Trilinear sampling: Eq. (1) along x on the four cell edges, then along y,
-// then along z, for each component (Sec. 3.3).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
-
-struct Cell {
-    int ix, iy, iz;
-    float v[8][3];  // corner (a, b, c) -> index a + 2b + 4c
-};
-
-// The 8 corner nodes of cell (ix, iy, iz), as four x-neighbour pairs. F4
-// nodes are one 16-byte load each; F3 nodes are three 4-byte loads each
-// (their 12-byte stride leaves no common alignment for wider loads; 16- and
-// 32-byte variants with in-register selection were measured slower).
-template <int LAYOUT>
-__device__ __forceinline__ void load_cell(const void *__restrict__ field, uint32_t nnx,
-                                          uint32_t nnxy, int ix, int iy, int iz,
-                                          float (&v)[8][3]) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t node = (uint32_t)ix + nnx * (uint32_t)(iy + b) + nnxy * (uint32_t)(iz + c);
-            const int k0 = 2 * b + 4 * c;
-            if (LAYOUT == LAYOUT_F4) {
-                const float4 *f = reinterpret_cast<const float4 *>(field) + node;
-                const float4 a0 = __ldg(f);
-                const float4 a1 = __ldg(f + 1);
-                v[k0][0] = a0.x; v[k0][1] = a0.y; v[k0][2] = a0.z;
-                v[k0 + 1][0] = a1.x; v[k0 + 1][1] = a1.y; v[k0 + 1][2] = a1.z;
-            } else {
-                const float *f = reinterpret_cast<const float *>(field) + 3ull * node;
-                v[k0][0] = __ldg(f + 0); v[k0][1] = __ldg(f + 1); v[k0][2] = __ldg(f + 2);
-                v[k0 + 1][0] = __ldg(f + 3); v[k0 + 1][1] = __ldg(f + 4); v[k0 + 1][2] = __ldg(f + 5);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float3 trilerp(const float (&v)[8][3], float fx, float fy, float fz) {
-    float r[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float c00 = lerp1(v[0][k], v[1][k], fx);
-        const float c10 = lerp1(v[2][k], v[3][k], fx);
-        const float c01 = lerp1(v[4][k], v[5][k], fx);
-        const float c11 = lerp1(v[6][k], v[7][k], fx);
-        const float c0 = lerp1(c00, c10, fy);
-        const float c1 = lerp1(c01, c11, fy);
-        r[k] = lerp1(c0, c1, fz);
-    }
-    return make_float3(r[0], r[1], r[2]);
-}
-
-// Block geometry held in registers while a group is processed.
-struct Geo {
-    int nx, ny, nz;        // cells
-    float fnx, fny, fnz;   // cells as float (closed-box test)
-    uint32_t nnx, nnxy;    // node strides
-};
-
-__device__ __forceinline__ Geo load_geo(const BlockDev &B) {
-    Geo g;
-    g.nx = B.n[0]; g.ny = B.n[1]; g.nz = B.n[2];
-    g.fnx = (float)g.nx; g.fny = (float)g.ny; g.fnz = (float)g.nz;
-    g.nnx = (uint32_t)B.nn[0];
-    g.nnxy = (uint32_t)B.nn[0] * (uint32_t)B.nn[1];
-    return g;
-}
-
-// Closed box [0, n] in cell coordinates; NaN compares false and so is outside.
-__device__ __forceinline__ bool inside(const Geo &g, float x, float y, float z) {
-    return x >= 0.f && x <= g.fnx && y >= 0.f && y <= g.fny && z >= 0.f && z <= g.fnz;
-}
-
-template <int LAYOUT>
-__device__ __forceinline__ float3 sample(Cell &C, const void *__restrict__ field, const Geo &g,
-                                         float x, float y, float z) {
-    // cell index clamp(floor(xi), 0, n-1): the upper face uses the last cell
-    const int ix = min(max(__float2int_rd(x), 0), g.nx - 1);
-    const int iy = min(max(__float2int_rd(y), 0), g.ny - 1);
-    const int iz = min(max(__float2int_rd(z), 0), g.nz - 1);
-    if (ix != C.ix || iy != C.iy || iz != C.iz) {
-        load_cell<LAYOUT>(field, g.nnx, g.nnxy, ix, iy, iz, C.v);
-        C.ix = ix; C.iy = iy; C.iz = iz;
-    }
-    return trilerp(C.v, x - (float)ix, y - (float)iy, z - (float)iz);
-}
-
-// One RK4 step in cell units (s = dt / h per axis). Returns false, leaving x
-// unchanged, as soon as a stage point or the end point leaves the block.
-template <int LAYOUT>
-__device__ __forceinline__ bool rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
-                                         const float3 s) {
-    const float3 hs = make_float3(0.5f * s.x, 0.5f * s.y, 0.5f * s.z);
-    Cell C;
-    C.ix = -1; C.iy = -1; C.iz = -1;
-    const float3 k1 = sample<LAYOUT>(C, field, g, x.x, x.y, x.z);
-    float px = fmaf(hs.x, k1.x, x.x), py = fmaf(hs.y, k1.y, x.y), pz = fmaf(hs.z, k1.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
-    const float3 k2 = sample<LAYOUT>(C, field, g, px, py, pz);
-    float3 acc = make_float3(k1.x + 2.f * k2.x, k1.y + 2.f * k2.y, k1.z + 2.f * k2.z);
-    px = fmaf(hs.x, k2.x, x.x); py = fmaf(hs.y, k2.y, x.y); pz = fmaf(hs.z, k2.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
-    const float3 k3 = sample<LAYOUT>(C, field, g, px, py, pz);
-    acc.x = fmaf(2.f, k3.x, acc.x); acc.y = fmaf(2.f, k3.y, acc.y); acc.z = fmaf(2.f, k3.z, acc.z);
-    px = fmaf(s.x, k3.x, x.x); py = fmaf(s.y, k3.y, x.y); pz = fmaf(s.z, k3.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
-    const float3 k4 = sample<LAYOUT>(C, field, g, px, py, pz);
-    acc.x += k4.x; acc.y += k4.y; acc.z += k4.z;
-    const float sx6 = s.x * (1.f / 6.f), sy6 = s.y * (1.f / 6.f), sz6 = s.z * (1.f / 6.f);
-    px = fmaf(sx6, acc.x, x.x); py = fmaf(sy6, acc.y, x.y); pz = fmaf(sz6, acc.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
-    x = make_float3(px, py, pz);
-    return true;
-}
 
 // Index of the block holding global slot/id i (blocks sorted by base).
 __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, int nb, int64_t i) {
