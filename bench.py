@@ -549,11 +549,172 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
             "global_particle_steps": count_particle_steps(gce, L),
         }
 
-    # (4) end to end: fields copied from pinned host memory every cycle,
+    # (4) adjoint and batched workloads against the plain path (rank 0)
+    if rank == 0:
+        res["adjoint"] = adjoint_leg(args, dev, stream)
+        res["batched"] = batched_leg(args, dev, stream)
+
+    # (5) end to end: fields copied from pinned host memory every cycle,
     # basis flows copied back every interval; copies overlap compute on a
     # second stream with a two-slot device ring.
     res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb)
     return res
+
+
+def adjoint_leg(args, dev, stream):
+    """Adjoint workload (64^3 ABC block on [0, 2 pi]^3, 32^3 seeds, 200 cycles,
+    dt 0.01, checkpoints every 16): the plain interval against the tape's
+    forward and forward + backward (seed and node-velocity gradients of
+    sum over valid particles of |end - seed|^2), same GPU, same fields."""
+    import torch
+    from paper_2004_02003_gb300 import adjoint, bto, inputs
+    n, L, dt, stride, K = (64, 64, 64), 200, 0.01, 2, 16
+    h = (2 * np.pi / 64,) * 3
+    F = torch.stack([inputs.abc_field_torch(n, (0, 0, 0), h, c * dt, dev) for c in range(L)]).contiguous()
+    ctx = bto.Context(n, (0, 0, 0), h, stride, L)
+    out = ctx.alloc_outputs(dev)
+
+    def plain():
+        for c in range(L):
+            ctx.advect(F[c], dt)
+        ctx.end_interval(out)
+
+    plain()
+    torch.cuda.synchronize()
+    seeds = out["seeds"].clone()
+    P = seeds.shape[0]
+    tape = adjoint.Tape(n, (0, 0, 0), h, P, L, K)
+
+    def fwd():
+        return adjoint.flow_map(seeds, F, tape, dt)
+
+    def fwd_bwd():
+        s = seeds.clone().requires_grad_(True)
+        Fg = F.detach().requires_grad_(True)
+        ends, valid, _ = adjoint.flow_map(s, Fg, tape, dt)
+        loss = (((ends - s) ** 2).sum(dim=1) * valid.to(torch.float32)).sum()
+        loss.backward()
+        return s.grad, Fg.grad
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(args.steps, 10))
+    t_plain = timed(plain, reps)
+    t_fwd = timed(fwd, reps)
+    t_fb = timed(fwd_bwd, reps)
+    ctx.check()
+    ex = out["exit_cycle"].cpu().numpy()
+    psteps = count_particle_steps(ex, L)
+    tape.close()
+    ctx.close()
+    return {"workload": "64^3 ABC on [0,2pi]^3, 32,768 seeds (stride 2), 200 cycles, dt 0.01, checkpoints every 16",
+            "plain_ms": t_plain, "tape_forward_ms": t_fwd, "forward_backward_ms": t_fb,
+            "forward_backward_vs_plain": t_fb / t_plain,
+            "plain_particle_steps_per_s": psteps / (t_plain / 1e3),
+            "valid_frac": float((ex < 0).mean())}
+
+
+def batched_layout(seed=20040206, nb=512):
+    """512 uneven blocks: a 16 x 8 x 4 arrangement of slots over
+    [0, 2] x [0, 1] x [0, 1]; block b fills its slot with n_a ~ U{16..96}
+    cells per axis (redrawn until max/min <= 3) and a seed stride drawn from
+    {1, 2, 4}."""
+    rng = np.random.default_rng(seed)
+    size = (2.0 / 16, 1.0 / 8, 1.0 / 4)
+    ext, org, spc, strides = [], [], [], []
+    for k in range(nb):
+        ix, iy, iz = k % 16, (k // 16) % 8, k // 128
+        while True:
+            n = rng.integers(16, 97, size=3)
+            if n.max() / n.min() <= 3:
+                break
+        ext.append(tuple(int(v) for v in n))
+        org.append((ix * size[0], iy * size[1], iz * size[2]))
+        spc.append(tuple(size[a] / int(n[a]) for a in range(3)))
+        strides.append(int(rng.choice([1, 2, 4])))
+    return ext, org, spc, strides
+
+
+def batched_leg(args, dev, stream):
+    """Batched workload: 512 uneven blocks in one persistent launch per cycle
+    (and as one CUDA graph per interval) against 512 single-block contexts,
+    after the native autotuner has picked the launch shape."""
+    import torch
+    from paper_2004_02003_gb300 import bto, inputs
+    ext, org, spc, strides = batched_layout()
+    nb, L, NF = len(ext), 64, 4
+    modes = inputs.fourier_modes(SEED + 2, m=32, kmin=1.0, kmax=16.0, drift_max=0.05)
+    vmax = np.pi * inputs.DG_A * 1.5 + 0.1      # bound of |u| (gyre + scaled turbulence)
+    dt = 0.25 * min(min(h) for h in spc) / vmax
+    fields = [[inputs.double_gyre_fourier_torch(modes, ext[b], org[b], spc[b], c * dt, c, dev)
+               for b in range(nb)] for c in range(NF)]
+    table = torch.tensor([fields[c % NF][b].data_ptr() for c in range(L) for b in range(nb)],
+                         dtype=torch.int64, device=dev)
+    nodes = sum((n[0] + 1) * (n[1] + 1) * (n[2] + 1) for n in ext)
+    ctx = bto.Context.batch(ext, org, spc, strides, L)
+    tune = ctx.autotune(table, 16, dt)
+    out = ctx.alloc_outputs(dev)
+
+    def run_batched():
+        for c in range(L):
+            ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+        ctx.end_interval(out)
+
+    def run_graph():
+        ctx.interval_graph(table, dt)
+        ctx.end_interval(out)
+
+    def timed(fn, reps, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, min(args.steps, 10))
+    t_b = timed(run_batched, reps)
+    ex = out["exit_cycle"].cpu().numpy()
+    psteps = count_particle_steps(ex, L)
+    t_g = timed(run_graph, reps)
+    ctx.check()
+    plain = [bto.Context(ext[b], org[b], spc[b], strides[b], L) for b in range(nb)]
+    pouts = [p.alloc_outputs(dev) for p in plain]
+
+    def run_plain():
+        for c in range(L):
+            for b in range(nb):
+                plain[b].advect(fields[c % NF][b], dt)
+        for b in range(nb):
+            plain[b].end_interval(pouts[b])
+
+    t_p = timed(run_plain, 1, warm=1)
+    for p in plain:
+        p.check()
+        p.close()
+    P = ctx.P
+    ctx.close()
+    return {"workload": "512 uneven blocks (16..96 cells per axis, aspect <= 3), strides {1,2,4}, "
+                        "double gyre + 32 Fourier modes, interval 64",
+            "blocks": nb, "particles": P, "nodes": nodes, "dt": dt, "autotune": tune,
+            "batched_value": psteps / (t_b / 1e3), "graph_value": psteps / (t_g / 1e3),
+            "plain_value": psteps / (t_p / 1e3), "batched_vs_plain": t_p / t_b,
+            "ms_per_interval": {"batched": t_b, "graph": t_g, "plain": t_p},
+            "terminated_frac": float((ex >= 0).mean())}
 
 
 def e2e(args, ctx, fields, dt, dev, stream, nb):

@@ -173,6 +173,21 @@ BTO_API bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta,
  * reg_cap, grid size). */
 BTO_API bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]);
 
+/* Autotuner: times every compiled launch shape of the advection kernel
+ * (threads 128/256 x particles per thread 1/2/4 x reg_cap 0/1) on this
+ * context's own blocks, and keeps the fastest. Each trial reseeds the
+ * interval, runs `cycles` cycles (1..interval_cycles) on the fields of
+ * d_field_table (DEVICE array of at least cycles*nb field pointers, entry
+ * c*nb + b for block b in cycle c, as for bto_launch_interval_graph) with
+ * step dt, and is timed with CUDA events on `stream`; the interval is
+ * reseeded at the end. Synchronises the stream (a set-up call). Only at
+ * cycle 0, else BTO_ERR_STATE. Outputs (host, optional): best[5] as
+ * bto_get_launch, ms[12] the mean time per cycle of each shape in the order
+ * above (threads slowest, reg_cap fastest). Results do not depend on the
+ * shape, only the speed does. */
+BTO_API bto_status bto_autotune(bto_ctx *ctx, const void *const *d_field_table, int32_t cycles,
+                                float dt, bto_stream stream, int32_t best[5], float ms[12]);
+
 /* Diagnostics (not for the per-cycle path): copy the active particle list as
  * it stands before the next cycle.
  *   d_out  P*4 floats (device); for block b, rows offsets[b] ..

@@ -57,6 +57,7 @@ def _declare(lib):
         "bto_launch_interval_graph": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
+        "bto_autotune": ([vp, vp, ctypes.c_int32, ctypes.c_float, vp, c_i32p, c_fp], ctypes.c_int),
         "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
         "bto_last_error": ([vp], ctypes.c_int),
         "bto_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -201,6 +202,20 @@ def bto_get_launch(ctx: int) -> dict:
             "reg_cap": buf[3], "grid": buf[4]}
 
 
+AUTOTUNE_SHAPES = [(t, p, c) for t in (128, 256) for p in (1, 2, 4) for c in (0, 1)]
+
+
+def bto_autotune(ctx: int, d_field_table, cycles: int, dt: float, stream=None) -> dict:
+    best = (ctypes.c_int32 * 5)()
+    ms = (ctypes.c_float * 12)()
+    _check(load().bto_autotune(ctx, _addr(d_field_table), int(cycles), float(dt), _stream(stream), best, ms),
+           "bto_autotune")
+    return {"best": {"threads_per_cta": best[0], "particles_per_thread": best[1], "ctas_per_sm": best[2],
+                     "reg_cap": best[3], "grid": best[4]},
+            "ms_per_cycle": {f"{t}x{p}{'c' if c else ''}": round(ms[k], 5)
+                             for k, (t, p, c) in enumerate(AUTOTUNE_SHAPES)}}
+
+
 def bto_copy_active(ctx: int, d_out, stream=None) -> list:
     nb = bto_num_blocks(ctx)
     live = (ctypes.c_int32 * nb)()
@@ -322,6 +337,9 @@ class Context:
         bto_end_interval(self.handle, out["seeds"], out["ends"], out["valid"],
                          out.get("exit_cycle"), stream)
         return out
+
+    def autotune(self, field_table, cycles, dt, stream=None):
+        return bto_autotune(self.handle, field_table, cycles, dt, stream)
 
     def copy_active(self, d_out, stream=None):
         return bto_copy_active(self.handle, d_out, stream)

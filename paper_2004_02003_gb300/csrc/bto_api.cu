@@ -428,6 +428,64 @@ bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]) {
     return BTO_OK;
 }
 
+bto_status bto_autotune(bto_ctx *ctx, const void *const *d_field_table, int32_t cycles, float dt,
+                        bto_stream stream, int32_t best[5], float ms[12]) {
+    if (!ctx || !d_field_table || !std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
+    if (cycles < 1 || cycles > ctx->L) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_field_table) % alignof(void *)) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int shapes[12][3] = {{128, 1, 0}, {128, 1, 1}, {128, 2, 0}, {128, 2, 1}, {128, 4, 0}, {128, 4, 1},
+                               {256, 1, 0}, {256, 1, 1}, {256, 2, 0}, {256, 2, 1}, {256, 4, 0}, {256, 4, 1}};
+    const int keep[4] = {ctx->nt, ctx->ppt, ctx->ctas_per_sm, ctx->cap ? 1 : 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BTO_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); (void)cudaGetLastError(); return cuda_status(ce); }
+    float best_ms = 0.f;
+    int best_k = -1;
+    bto_status st = BTO_OK;
+    for (int k = 0; k < 12 && st == BTO_OK; ++k) {
+        ctx->nt = shapes[k][0];
+        ctx->ppt = shapes[k][1];
+        ctx->ctas_per_sm = 0;
+        ctx->cap = shapes[k][2] != 0;
+        st = configure_launch(ctx);
+        if (st == BTO_OK) st = seed(ctx, s);
+        if (st != BTO_OK) break;
+        ce = cudaEventRecord(e0, s);
+        for (int32_t c = 0; c < cycles && st == BTO_OK && ce == cudaSuccess; ++c)
+            st = advect_impl(ctx, nullptr, d_field_table + (size_t)c * ctx->nb, dt, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+        if (ce != cudaSuccess) { st = cuda_status(ce); (void)cudaGetLastError(); break; }
+        t /= (float)cycles;
+        if (ms) ms[k] = t;
+        if (best_k < 0 || t < best_ms) { best_ms = t; best_k = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == BTO_OK && best_k >= 0) {
+        ctx->nt = shapes[best_k][0];
+        ctx->ppt = shapes[best_k][1];
+        ctx->ctas_per_sm = 0;
+        ctx->cap = shapes[best_k][2] != 0;
+    } else {
+        ctx->nt = keep[0]; ctx->ppt = keep[1]; ctx->ctas_per_sm = keep[2]; ctx->cap = keep[3] != 0;
+    }
+    const bto_status st2 = configure_launch(ctx);
+    drop_graph(ctx);
+    const bto_status st3 = seed(ctx, s);
+    BTO_CUDA(cudaStreamSynchronize(s));
+    if (st != BTO_OK) return st;
+    if (st2 != BTO_OK) return st2;
+    if (st3 != BTO_OK) return st3;
+    if (best) return bto_get_launch(ctx, best);
+    return BTO_OK;
+}
+
 bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream stream) {
     if (!ctx || !d_out || !live) return BTO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_out) % 16) return BTO_ERR_INVALID_ARG;

@@ -60,6 +60,44 @@ def abc_field(n, origin, h, t: float, eps: float = 0.1) -> np.ndarray:
     return _pack(ux, uy, uz)
 
 
+def abc_field_torch(n, origin, h, t: float, device, eps: float = 0.1):
+    """Same field as :func:`abc_field`, evaluated with torch on ``device`` in
+    float64 and rounded to float32."""
+    import torch
+    x, y, z = (torch.as_tensor(v, dtype=torch.float64, device=device) for v in node_coords(n, origin, h))
+    s = eps * np.sin(2.0 * np.pi * t)
+    Z, Y, X = torch.meshgrid(z, y, x, indexing="ij")
+    ux = ABC_A * torch.sin(Z + s) + ABC_C * torch.cos(Y + s)
+    uy = ABC_B * torch.sin(X + s) + ABC_A * torch.cos(Z + s)
+    uz = ABC_C * torch.sin(Y + s) + ABC_B * torch.cos(X + s)
+    return torch.stack([ux, uy, uz], dim=-1).to(torch.float32).contiguous()
+
+
+DG_A, DG_EPS, DG_OMEGA = 0.1, 0.25, 2.0 * np.pi / 10.0
+
+
+def double_gyre_fourier_torch(modes: "FourierModes", n, origin, h, t: float, cycle: int, device,
+                              turb: float = 0.1):
+    """Double gyre in (x, y) (the Shadden et al. form: stream function
+    A sin(pi f(x, t)) sin(pi y), f = a x^2 + b x, a = eps sin(omega t),
+    b = 1 - 2 eps sin(omega t), A = 0.1, eps = 0.25, omega = 2 pi / 10, on
+    [0, 2] x [0, 1]), constant in z, plus ``turb`` times the Fourier-mode
+    turbulence of ``modes`` at ``cycle`` (which supplies the z component).
+    Evaluated with torch in float64 on ``device``, rounded to float32."""
+    import torch
+    x, y, z = (torch.as_tensor(v, dtype=torch.float64, device=device) for v in node_coords(n, origin, h))
+    a = DG_EPS * np.sin(DG_OMEGA * t)
+    b = 1.0 - 2.0 * DG_EPS * np.sin(DG_OMEGA * t)
+    Y, X = torch.meshgrid(y, x, indexing="ij")
+    f = a * X * X + b * X
+    u = -np.pi * DG_A * torch.sin(np.pi * f) * torch.cos(np.pi * Y)
+    v = np.pi * DG_A * torch.cos(np.pi * f) * torch.sin(np.pi * Y) * (2.0 * a * X + b)
+    out = turb * fourier_field_torch(modes, n, origin, h, cycle, device).to(torch.float64)
+    out[..., 0] += u[None]
+    out[..., 1] += v[None]
+    return out.to(torch.float32).contiguous()
+
+
 def uniform_field(n, vel) -> np.ndarray:
     shape = (int(n[2]) + 1, int(n[1]) + 1, int(n[0]) + 1, 3)
     out = np.empty(shape, dtype=np.float32)

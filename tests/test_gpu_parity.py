@@ -405,3 +405,35 @@ def test_last_node_pairs_near_array_end():
     gpu = run_gpu_interval(ctx, _dev([f] * L), dt)
     compare(gpu, ref, h)
     ctx.close()
+
+
+def test_autotune_keeps_results_and_reports_every_shape():
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt = 6, 0.006
+    modes = inputs.fourier_modes(12, m=8, kmax=5.0)
+    devf = [_dev([inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(len(ext))])
+            for c in range(L)]
+    table = torch.tensor([t.data_ptr() for fc in devf for t in fc], dtype=torch.int64, device="cuda")
+    nb = len(ext)
+    ref = bto.Context.batch(ext, origins, spac, strides, L)
+    for c in range(L):
+        ref.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    r0 = {k: v.cpu().numpy() for k, v in ref.end_interval().items()}
+    ctx = bto.Context.batch(ext, origins, spac, strides, L)
+    ctx.advect_batch(table[:nb], dt)
+    with pytest.raises(bto.BtoError) as e:                 # only at cycle 0
+        ctx.autotune(table, L, dt)
+    assert e.value.status == bto.BTO_ERR_STATE
+    ctx.close()
+    ctx = bto.Context.batch(ext, origins, spac, strides, L)
+    rep = ctx.autotune(table, L, dt)
+    assert len(rep["ms_per_cycle"]) == 12 and all(v > 0 for v in rep["ms_per_cycle"].values())
+    assert ctx.launch() == rep["best"]
+    for c in range(L):
+        ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    r1 = {k: v.cpu().numpy() for k, v in ctx.end_interval().items()}
+    for k in r0:
+        assert np.array_equal(r0[k], r1[k]), k
+    ref.check(); ctx.check()
+    ref.close(); ctx.close()
