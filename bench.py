@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/graph/global-map/e2e legs")
+    ap.add_argument("--no-large", action="store_true", help="skip the 134M-particle in situ emulation leg")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--layout", default="f3", choices=["f3", "f4"],
                     help="field layout handed to the library (f4 pads each node to 16 bytes)")
@@ -328,6 +329,11 @@ def run_ours(args):
     ctx.set_layout(layout)
     if args.launch:
         ctx.set_launch(*[int(v) for v in args.launch.split(",")])
+        tune = None
+    else:
+        # the library's autotuner picks the launch shape on this workload
+        # (each of its 12 shapes runs one whole interval; then reseeded)
+        tune = ctx.autotune(table, L, dt)
     P = ctx.P
     out = ctx.alloc_outputs(dev)
 
@@ -421,6 +427,7 @@ def run_ours(args):
             "field_layout": args.layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
             "l2": f"inputs larger than L2: each cycle reads a 206 MB field; {nf} distinct fields resident",
             "launch": ctx.launch(),
+            "autotune_ms_per_cycle": tune["ms_per_cycle"] if tune else None,
             "parallelism": f"weak: {world} rank(s), each the full workload, no collective",
         },
         "units_per_step": psteps,
@@ -464,10 +471,10 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     res = {}
     # (1) plain: one single-block context per block, one launch per block and cycle
     plain = [bto.Context(ext[b], org[b], spc[b], STRIDE, L) for b in range(nb)]
+    shape = ctx.launch()
     for p in plain:
         p.set_layout(ctx_layout(args))
-        if args.launch:
-            p.set_launch(*[int(v) for v in args.launch.split(",")])
+        p.set_launch(shape["threads_per_cta"], shape["particles_per_thread"], 0, shape["reg_cap"])
     outs = [p.alloc_outputs(dev) for p in plain]
 
     def plain_step():
@@ -493,8 +500,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     # (2) graph: the interval's cycles as one CUDA graph
     g = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
     g.set_layout(ctx_layout(args))
-    if args.launch:
-        g.set_launch(*[int(v) for v in args.launch.split(",")])
+    g.set_launch(shape["threads_per_cta"], shape["particles_per_thread"], 0, shape["reg_cap"])
     gout = g.alloc_outputs(dev)
     for _ in range(max(1, args.warmup)):
         g.interval_graph(table, dt)
@@ -553,6 +559,8 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     if rank == 0:
         res["adjoint"] = adjoint_leg(args, dev, stream)
         res["batched"] = batched_leg(args, dev, stream)
+        if not args.no_large:
+            res["large"] = large_leg(args, dev, stream)
 
     # (5) end to end: fields copied from pinned host memory every cycle,
     # basis flows copied back every interval; copies overlap compute on a
@@ -715,6 +723,99 @@ def batched_leg(args, dev, stream):
             "plain_value": psteps / (t_p / 1e3), "batched_vs_plain": t_p / t_b,
             "ms_per_interval": {"batched": t_b, "graph": t_g, "plain": t_p},
             "terminated_frac": float((ex >= 0).mean())}
+
+
+def large_leg(args, dev, stream, nf=10):
+    """Large in situ emulation: a 512^3-cell domain as 4 x 4 x 4 blocks of 128^3
+    cells, one seed per cell (134,217,728 particles), 128 Fourier modes,
+    dt = 0.2 cell / max|u|, 3 intervals of 50 cycles; the batched form (one
+    launch per cycle) and the plain form (64 contexts, 64 launches per cycle)
+    side by side, and each interval against the global flow map (one block
+    over the whole domain: particles cross the block faces). The fields of
+    nf distinct cycles are resident (cycle c uses field c % nf), each 1.65 GB
+    for the blocks and 1.62 GB for the global grid."""
+    import torch
+    from paper_2004_02003_gb300 import bto, inputs
+    G, n, S, L, NI = 512, 128, 1, 50, 3
+    h = 1.0 / G
+    dt = 0.2 * h
+    nbx = G // n
+    modes = inputs.fourier_modes(SEED + 4, m=128, kmin=1.0, kmax=16.0, drift_max=0.05)
+    blocks = [(bx, by, bz) for bz in range(nbx) for by in range(nbx) for bx in range(nbx)]
+    ext = [(n, n, n)] * len(blocks)
+    org = [(b[0] * n * h, b[1] * n * h, b[2] * n * h) for b in blocks]
+    spc = [(h, h, h)] * len(blocks)
+    nb = len(blocks)
+    gfields, bfields = [], []
+    for c in range(nf):
+        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), c, dev)
+        gfields.append(gf)
+        bfields.append([gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous()
+                        for (bx, by, bz) in blocks])
+    torch.cuda.synchronize()
+    bctx = bto.Context.batch(ext, org, spc, [S] * nb, L)
+    gctx = bto.Context((G, G, G), (0, 0, 0), (h, h, h), S, L)
+    plain = [bto.Context(ext[b], org[b], spc[b], S, L) for b in range(nb)]
+    bout, gout = bctx.alloc_outputs(dev), gctx.alloc_outputs(dev)
+    pouts = [p.alloc_outputs(dev) for p in plain]
+    def fidx(k, c):             # resident field of interval k, cycle c
+        return (k + c) % nf
+
+    tables = [torch.tensor([bfields[fidx(k, c)][b].data_ptr() for c in range(L) for b in range(nb)],
+                           dtype=torch.int64, device=dev) for k in range(NI)]
+    # global id of each block seed (stride 1: seeds are the block's nodes)
+    j = torch.arange(n ** 3, device=dev)
+    jx, jy, jz = j % n, (j // n) % n, j // (n * n)
+    gid = torch.cat([(jx + b[0] * n) + G * ((jy + b[1] * n) + G * (jz + b[2] * n)) for b in blocks])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_b = t_p = 0.0
+    report = []
+    psteps_total = 0
+    for k in range(NI):
+        ev[0].record(stream)
+        for c in range(L):
+            bctx.advect_batch(tables[k][c * nb:(c + 1) * nb], dt)
+        bctx.end_interval(bout)
+        ev[1].record(stream)
+        for c in range(L):
+            for b in range(nb):
+                plain[b].advect(bfields[fidx(k, c)][b], dt)
+        for b in range(nb):
+            plain[b].end_interval(pouts[b])
+        ev[2].record(stream)
+        for c in range(L):
+            gctx.advect(gfields[fidx(k, c)], dt)
+        gctx.end_interval(gout)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t_b += ev[0].elapsed_time(ev[1])
+        t_p += ev[1].elapsed_time(ev[2])
+        bv = bout["valid"] == 1
+        gv = gout["valid"][gid] == 1
+        d = ((bout["ends"][bv] - gout["ends"][gid][bv]).abs().amax(dim=1) / h).double()
+        q = torch.quantile(d[torch.randperm(d.numel(), device=dev)[:1 << 24]],
+                           torch.tensor([0.5, 0.99, 0.9999], dtype=torch.float64, device=dev)).tolist()
+        dev_max = d.max().item()
+        ex = bout["exit_cycle"].cpu().numpy()
+        psteps_total += count_particle_steps(ex, L)
+        report.append({"interval": k, "terminated_frac_bto": float(1 - bv.float().mean().item()),
+                       "terminated_frac_global": float(1 - (gout["valid"] == 1).float().mean().item()),
+                       "bto_valid_not_global_valid": int((bv & ~gv).sum().item()),
+                       "max_valid_end_deviation_cells": dev_max,
+                       "valid_end_deviation_cells_p50_p99_p9999": q,
+                       "global_ms": ev[2].elapsed_time(ev[3])})
+    for p in plain:
+        p.check()
+    bctx.check(); gctx.check()
+    P = bctx.P
+    for p in plain:
+        p.close()
+    bctx.close(); gctx.close()
+    return {"workload": "512^3 cells as 4x4x4 blocks of 128^3, 1 seed per cell, 128 Fourier modes, "
+                        "3 intervals of 50 cycles, dt = 0.2 cell/max|u|",
+            "particles": P, "resident_fields": nf,
+            "batched_value": psteps_total / (t_b / 1e3), "plain_value": psteps_total / (t_p / 1e3),
+            "batched_ms_per_interval": t_b / NI, "plain_ms_per_interval": t_p / NI, "intervals": report}
 
 
 def e2e(args, ctx, fields, dt, dev, stream, nb):

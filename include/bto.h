@@ -160,8 +160,8 @@ BTO_API bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_
 
 /* Launch shape of the advection kernel: threads per CTA (128 or 256),
  * particles per thread (1, 2 or 4; a warp owns 32*ppt list slots), CTAs per
- * SM (0 = as many as fit) and reg_cap (1 = registers capped at 64 per
- * thread so that 1024 threads fit on an SM; 0 = no cap). Results do not
+ * SM (0 = as many as fit) and reg_cap (1 = registers capped at 80 per
+ * thread so that 768 threads fit on an SM; 0 = no cap). Results do not
  * depend on the shape. Only at cycle 0 (between intervals), else
  * BTO_ERR_STATE; changing particles_per_thread reseeds the interval
  * (synchronously). */

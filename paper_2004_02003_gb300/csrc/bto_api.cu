@@ -34,7 +34,7 @@ struct bto_ctx {
     int32_t cycle = 0;        // cycles advanced in the current interval
     int layout = bto::LAYOUT_F3;
     int nt = 128, ppt = 2, ctas_per_sm = 0, grid = 0;
-    bool cap = false;         // cap registers at 64 (1024 threads per SM)
+    bool cap = false;         // cap registers at 80 (768 threads per SM)
     size_t dyn_smem = 0;
     std::vector<BlockDev> blocks_h;
     BlockDev *blocks = nullptr;

@@ -214,11 +214,11 @@ cudaError_t occ_t(size_t dyn, int *n) {
 }
 
 // Dispatch over the compiled launch shapes: threads per CTA, particles per
-// thread, and whether registers are capped at 64 (1024 threads per SM).
+// thread, and whether registers are capped at 80 (768 threads per SM).
 #define BTO_SHAPES(X, L, B)                                                                  \
     X(L, 128, 1, B, 1) X(L, 128, 2, B, 1) X(L, 128, 4, B, 1) X(L, 256, 1, B, 1)                \
-    X(L, 256, 2, B, 1) X(L, 256, 4, B, 1) X(L, 128, 1, B, 8) X(L, 128, 2, B, 8)                \
-    X(L, 128, 4, B, 8) X(L, 256, 1, B, 4) X(L, 256, 2, B, 4) X(L, 256, 4, B, 4)
+    X(L, 256, 2, B, 1) X(L, 256, 4, B, 1) X(L, 128, 1, B, 6) X(L, 128, 2, B, 6)                \
+    X(L, 128, 4, B, 6) X(L, 256, 1, B, 3) X(L, 256, 2, B, 3) X(L, 256, 4, B, 3)
 
 }  // namespace
 
