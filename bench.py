@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--layout", default="f3", choices=["f3", "f4"],
                     help="field layout handed to the library (f4 pads each node to 16 bytes)")
+    ap.add_argument("--ingest", action="store_true", help="repack F3 fields to 16-byte nodes per block (H1)")
     ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
     ap.add_argument("--fields", type=int, default=INTERVAL,
                     help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
@@ -327,6 +328,8 @@ def run_ours(args):
     ctx = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
     layout = bto.BTO_FIELD_F4_AOS if args.layout == "f4" else bto.BTO_FIELD_F3_AOS
     ctx.set_layout(layout)
+    if args.ingest:
+        ctx.set_ingest(1)
     if args.launch:
         ctx.set_launch(*[int(v) for v in args.launch.split(",")])
         tune = None
@@ -425,6 +428,7 @@ def run_ours(args):
                         "stride 2 (2,097,152 particles), interval 100, dt=0.25 cell/max|u|",
             "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
             "field_layout": args.layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
+            "ingest": bool(args.ingest),
             "l2": f"inputs larger than L2: each cycle reads a 206 MB field; {nf} distinct fields resident",
             "launch": ctx.launch(),
             "autotune_ms_per_cycle": tune["ms_per_cycle"] if tune else None,

@@ -108,6 +108,17 @@ BTO_API bto_status bto_batch_create(int32_t nb, const int32_t *extents,
  * BTO_FIELD_F3_AOS). Only between intervals (cycle 0), else BTO_ERR_STATE. */
 BTO_API bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout);
 
+/* Field ingest (enable = 1): with F3_AOS fields, each cycle first repacks
+ * every block's field into a 16-byte-per-node buffer owned by the context
+ * (two buffers, block b+1 repacked on an internal stream while block b is
+ * advected on the caller's stream) and the advection gathers one 16-byte
+ * load per node from it. Results are identical with and without ingest.
+ * Allocates 2 x (largest block's nodes) x 16 bytes on first use. Only at
+ * cycle 0 and with the F3_AOS layout, else BTO_ERR_STATE; not available
+ * with bto_launch_interval_graph (BTO_ERR_UNSUPPORTED). enable = 0 goes
+ * back to gathering from the caller's F3 field directly (the default). */
+BTO_API bto_status bto_set_ingest(bto_ctx *ctx, int32_t enable);
+
 /* Total number of seeds P of the context (all blocks), or -1 for NULL. */
 BTO_API int64_t bto_num_seeds(const bto_ctx *ctx);
 

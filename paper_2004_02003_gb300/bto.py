@@ -48,6 +48,7 @@ def _declare(lib):
         "bto_batch_create": ([ctypes.c_int32, c_i32p, c_fp, c_fp, c_i32p, ctypes.c_int32,
                               ctypes.POINTER(vp)], ctypes.c_int),
         "bto_set_field_layout": ([vp, ctypes.c_int], ctypes.c_int),
+        "bto_set_ingest": ([vp, ctypes.c_int32], ctypes.c_int),
         "bto_num_seeds": ([vp], ctypes.c_int64),
         "bto_num_blocks": ([vp], ctypes.c_int32),
         "bto_batch_offsets": ([vp, c_i64p], ctypes.c_int),
@@ -153,6 +154,10 @@ def bto_batch_create(extents, origins, spacings, strides, interval_cycles: int) 
 
 def bto_set_field_layout(ctx: int, layout: int) -> None:
     _check(load().bto_set_field_layout(ctx, int(layout)), "bto_set_field_layout")
+
+
+def bto_set_ingest(ctx: int, enable: int) -> None:
+    _check(load().bto_set_ingest(ctx, int(enable)), "bto_set_ingest")
 
 
 def bto_num_seeds(ctx: int) -> int:
@@ -308,6 +313,9 @@ class Context:
 
     def set_layout(self, layout):
         bto_set_field_layout(self.handle, layout)
+
+    def set_ingest(self, enable):
+        bto_set_ingest(self.handle, int(enable))
 
     def set_launch(self, threads, ppt, ctas_per_sm=0, reg_cap=0):
         bto_set_launch(self.handle, threads, ppt, ctas_per_sm, reg_cap)

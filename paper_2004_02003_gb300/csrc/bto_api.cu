@@ -51,6 +51,11 @@ struct bto_ctx {
     float gdt = 0.f;
     int gshape[5] = {0, 0, 0, 0, 0};
     cudaStream_t capture_stream = nullptr;
+    // H1 ingest (F3 fields repacked to F4 per block, two buffers in flight)
+    bool ingest = false;
+    float4 *f4buf[2] = {nullptr, nullptr};
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ing_done[2] = {nullptr, nullptr}, adv_done[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -115,6 +120,14 @@ void free_ctx(bto_ctx *c) {
     cudaFree(c->gcnt[1]);
     cudaFree(c->term);
     cudaFree(c->diag_dst);
+    cudaFree(c->f4buf[0]);
+    cudaFree(c->f4buf[1]);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ing_done[k]) cudaEventDestroy(c->ing_done[k]);
+        if (c->adv_done[k]) cudaEventDestroy(c->adv_done[k]);
+    }
     delete c;
 }
 
@@ -241,10 +254,58 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     return BTO_OK;
 }
 
+// One cycle with H1 ingest: block by block, the F3 field is repacked into
+// an F4 buffer on a side stream while the previous block is advected on the
+// caller's stream from the other buffer (events order the two).
+bto_status advect_ingest(bto_ctx *c, const void *field, const void *const *fields, float dt,
+                         cudaStream_t s) {
+    const int cyc = c->cycle;
+    const int G = group_size(c);
+    const int aux = (int)std::max<int64_t>(1, (int64_t)c->sm_count * 4);
+    BTO_CUDA(cudaEventRecord(c->ev_start, s));
+    BTO_CUDA(cudaStreamWaitEvent(c->side, c->ev_start, 0));
+    for (int32_t b = 0; b < c->nb; ++b) {
+        const BlockDev &B = c->blocks_h[(size_t)b];
+        const int64_t nodes = (int64_t)B.nn[0] * B.nn[1] * B.nn[2];
+        const int k = b & 1;
+        if (b >= 2) BTO_CUDA(cudaStreamWaitEvent(c->side, c->adv_done[k], 0));
+        BTO_CUDA(bto::launch_ingest(field, fields, b, nodes, c->f4buf[k], aux, c->side));
+        BTO_CUDA(cudaEventRecord(c->ing_done[k], c->side));
+        BTO_CUDA(cudaStreamWaitEvent(s, c->ing_done[k], 0));
+        const int64_t region = (b + 1 < c->nb ? c->blocks_h[(size_t)b + 1].slot_base : c->slots) - B.slot_base;
+        bto::AdvectArgs a;
+        a.blocks = c->blocks + b;
+        a.gblock = c->gblock;
+        a.nb = 1;
+        a.cycle = cyc;
+        a.field = c->f4buf[k];
+        a.fields = nullptr;
+        a.in = c->act[cyc & 1] + B.slot_base;
+        a.out = c->act[(cyc + 1) & 1] + B.slot_base;
+        a.gcnt_in = c->gcnt[cyc & 1] + B.slot_base / G;
+        a.gcnt_out = c->gcnt[(cyc + 1) & 1] + B.slot_base / G;
+        a.ngroups = region / G;
+        a.term = c->term;
+        a.dt = dt;
+        const int64_t need = (a.ngroups + c->nt / 32 - 1) / (c->nt / 32);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid, need));
+        cudaError_t e = bto::launch_advect(a, bto::LAYOUT_F4, c->nt, c->ppt, c->cap, grid, 0, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->sticky = cuda_status(e);
+            return c->sticky;
+        }
+        BTO_CUDA(cudaEventRecord(c->adv_done[k], s));
+    }
+    c->cycle = cyc + 1;
+    return BTO_OK;
+}
+
 bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields, float dt,
                        cudaStream_t s) {
     if (!std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
     if (c->cycle >= c->L) return BTO_ERR_STATE;
+    if (c->ingest) return advect_ingest(c, field, fields, dt, s);
     const int cyc = c->cycle;
     bto::AdvectArgs a;
     a.blocks = c->blocks;
@@ -290,10 +351,33 @@ bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout) {
     if (!ctx) return BTO_ERR_INVALID_ARG;
     if (layout != BTO_FIELD_F3_AOS && layout != BTO_FIELD_F4_AOS) return BTO_ERR_INVALID_ARG;
     if (ctx->cycle != 0) return BTO_ERR_STATE;
+    if (ctx->ingest && layout != BTO_FIELD_F3_AOS) return BTO_ERR_STATE;
     const int old = ctx->layout;
     ctx->layout = layout == BTO_FIELD_F4_AOS ? bto::LAYOUT_F4 : bto::LAYOUT_F3;
     bto_status st = configure_launch(ctx);
     if (st != BTO_OK) { ctx->layout = old; configure_launch(ctx); return st; }
+    drop_graph(ctx);
+    return BTO_OK;
+}
+
+bto_status bto_set_ingest(bto_ctx *ctx, int32_t enable) {
+    if (!ctx || (enable != 0 && enable != 1)) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    if (enable && ctx->layout != bto::LAYOUT_F3) return BTO_ERR_STATE;
+    if (enable && !ctx->f4buf[0]) {
+        int64_t maxn = 0;
+        for (const BlockDev &B : ctx->blocks_h)
+            maxn = std::max<int64_t>(maxn, (int64_t)B.nn[0] * B.nn[1] * B.nn[2]);
+        BTO_CUDA(cudaMalloc(&ctx->f4buf[0], sizeof(float4) * (size_t)maxn));
+        BTO_CUDA(cudaMalloc(&ctx->f4buf[1], sizeof(float4) * (size_t)maxn));
+        BTO_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        BTO_CUDA(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+        for (int k = 0; k < 2; ++k) {
+            BTO_CUDA(cudaEventCreateWithFlags(&ctx->ing_done[k], cudaEventDisableTiming));
+            BTO_CUDA(cudaEventCreateWithFlags(&ctx->adv_done[k], cudaEventDisableTiming));
+        }
+    }
+    ctx->ingest = enable != 0;
     drop_graph(ctx);
     return BTO_OK;
 }
@@ -329,6 +413,7 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
     if (!ctx || !d_field_table || !std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_field_table) % alignof(void *)) return BTO_ERR_INVALID_ARG;
     if (ctx->cycle != 0) return BTO_ERR_STATE;
+    if (ctx->ingest) return BTO_ERR_UNSUPPORTED;
     const bool same = ctx->gexec && ctx->gtable == d_field_table && ctx->gdt == dt &&
                       ctx->gshape[0] == ctx->layout && ctx->gshape[1] == ctx->nt &&
                       ctx->gshape[2] == ctx->ppt && ctx->gshape[3] == ctx->grid &&

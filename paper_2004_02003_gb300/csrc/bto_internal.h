@@ -64,6 +64,8 @@ cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, con
                               uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s);
 cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
                                int64_t slots, int group, float4 *out, int grid, cudaStream_t s);
+cudaError_t launch_ingest(const void *field, const void *const *fields, int b, int64_t nodes, float4 *out,
+                          int grid, cudaStream_t s);
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,
                               float *seeds, float *ends, uint8_t *valid, int32_t *exit_cycle,
                               int grid, cudaStream_t s);

@@ -201,6 +201,35 @@ __global__ void gather_live_kernel(const float4 *__restrict__ act, const int32_t
     }
 }
 
+// H1 ingest: repack one block's F3 field (12 bytes per node) into F4 (16 bytes
+// per node, pad 0) so that the advection kernel can gather a node with one
+// 16-byte load. Four nodes per thread: three 16-byte loads of 48 contiguous
+// bytes, four 16-byte stores (scalar loads when the field is not 16-byte
+// aligned and for the last nodes).
+__global__ void ingest_f3_f4_kernel(const void *__restrict__ field, const void *const *__restrict__ fields,
+                                    int b, int64_t nodes, float4 *__restrict__ out) {
+    const float *f = reinterpret_cast<const float *>(field ? field : fields[b]);
+    const bool vec = (reinterpret_cast<uintptr_t>(f) & 15u) == 0;
+    const int64_t quads = nodes / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += stride) {
+        float v[12];
+        if (vec) {
+            const float4 *p = reinterpret_cast<const float4 *>(f) + 3 * q;
+            const float4 a = __ldcs(p), bb = __ldcs(p + 1), c = __ldcs(p + 2);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = bb.x; v[5] = bb.y;
+            v[6] = bb.z; v[7] = bb.w; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) v[k] = __ldcs(f + 12 * q + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[4 * q + k] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 0.f);
+    }
+    for (int64_t i = quads * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += stride)
+        out[i] = make_float4(__ldcs(f + 3 * i), __ldcs(f + 3 * i + 1), __ldcs(f + 3 * i + 2), 0.f);
+}
+
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 cudaError_t launch_t(const AdvectArgs &a, int grid, size_t dyn, cudaStream_t s) {
     advect_kernel<LAYOUT, NT, PPT, BATCHED, MINB><<<grid, NT, dyn, s>>>(a);
@@ -267,6 +296,12 @@ cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, con
 cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
                                int64_t slots, int group, float4 *out, int grid, cudaStream_t s) {
     gather_live_kernel<<<grid, 256, 0, s>>>(act, gcnt, dst, slots, group, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest(const void *field, const void *const *fields, int b, int64_t nodes, float4 *out,
+                          int grid, cudaStream_t s) {
+    ingest_f3_f4_kernel<<<grid, 256, 0, s>>>(field, fields, b, nodes, out);
     return cudaGetLastError();
 }
 

@@ -436,3 +436,43 @@ def test_autotune_keeps_results_and_reports_every_shape():
         assert np.array_equal(r0[k], r1[k]), k
     ref.check(); ctx.check()
     ref.close(); ctx.close()
+
+
+def test_ingest_gives_identical_results():
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt = 10, 0.006
+    modes = inputs.fourier_modes(13, m=12, kmax=5.0)
+    devf = [_dev([inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(len(ext))])
+            for c in range(L)]
+    table = torch.tensor([t.data_ptr() for fc in devf for t in fc], dtype=torch.int64, device="cuda")
+    nb = len(ext)
+    outs = []
+    for ingest in (0, 1):
+        ctx = bto.Context.batch(ext, origins, spac, strides, L)
+        ctx.set_ingest(ingest)
+        for rep in range(2):                          # two intervals: buffers reused
+            for c in range(L):
+                ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+            outs.append({k: v.cpu().numpy() for k, v in ctx.end_interval().items()})
+        if ingest:
+            with pytest.raises(bto.BtoError) as e:
+                ctx.interval_graph(table, dt)
+            assert e.value.status == bto.BTO_ERR_UNSUPPORTED
+            with pytest.raises(bto.BtoError):
+                ctx.set_layout(bto.BTO_FIELD_F4_AOS)
+        ctx.check()
+        ctx.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[2][k]) and np.array_equal(outs[1][k], outs[3][k]), k
+    # single block as well
+    n, h, s_ = (30, 26, 22), (0.03, 0.035, 0.04), 1
+    fields = [inputs.fourier_field(modes, n, (0, 0, 0), h, c) for c in range(L)]
+    res = []
+    for ingest in (0, 1):
+        ctx = bto.Context(n, (0, 0, 0), h, s_, L)
+        ctx.set_ingest(ingest)
+        res.append(run_gpu_interval(ctx, _dev(fields), dt))
+        ctx.close()
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]), k
