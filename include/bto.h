@@ -157,6 +157,21 @@ BTO_API bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends,
                             uint8_t *d_valid, int32_t *d_exit_cycle,
                             bto_stream stream);
 
+/* bto_end_interval plus the termination locations (storing them is the
+ * paper's stated future work, Sec. 6; a reading of this library):
+ *   d_exit_pos   P*3 floats or NULL: for a terminated particle, the point
+ *                where the chord from its last in-block position to the
+ *                first tested point found outside (p2, p3, p4 or end
+ *                point) leaves the closed block; NaN for valid particles
+ *   d_exit_time  P floats or NULL: the matching time in cycles from the
+ *                start of the interval, c + t * f, with c the exit cycle,
+ *                t in [0, 1] the clipped fraction of the chord and f = 1/2
+ *                for p2/p3, 1 for p4 and the end point; NaN if valid
+ * Other arguments, errors and the reseed as in bto_end_interval. */
+BTO_API bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends,
+                                       uint8_t *d_valid, int32_t *d_exit_cycle,
+                                       float *d_exit_pos, float *d_exit_time, bto_stream stream);
+
 /* Capture the cycles of one interval of a context into a CUDA graph and
  * launch it on `stream`; later intervals relaunch the cached graph.
  *   d_field_table  DEVICE array of interval_cycles*nb device pointers,
@@ -215,6 +230,46 @@ BTO_API bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live,
  * failure or a device-side error word); waits for the context's last stream
  * work; clears the sticky state. */
 BTO_API bto_status bto_last_error(bto_ctx *ctx);
+
+/* ---- Post hoc reconstruction (Sec. 3.2, Sec. 3.3 Eq. 2) -----------------
+ *
+ * Lattice stand-in for the paper's Delaunay + barycentric reconstruction:
+ * basis flows on a lattice in canonical order (index jx + Sx*(jy + Sy*jz)),
+ * for instance the union of the blocks' seed lattices of a decomposed
+ * domain. A missing entry (valid = 0) takes, along the axis whose nearest
+ * valid neighbours on both sides are closest (a + b smallest; ties x, then
+ * y, then z), the linear interpolant (Eq. 1) of their end positions:
+ * end(J) = (b end(J - a) + a end(J + b)) / (a + b). Eq. (2) shows that
+ * interpolating through such a filled value equals interpolating from the
+ * two neighbours. Entries with no such axis stay missing (NaN).
+ *   lattice[3]  Sx, Sy, Sz >= 1 (host)
+ *   d_ends      P*3 floats; entries with valid = 0 are ignored
+ *   d_valid     P bytes
+ *   d_out       P*3 floats written (must not overlap d_ends)
+ *   d_status    P bytes or NULL: 1 = valid, 2 = filled, 0 = still missing */
+BTO_API bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_ends,
+                                    const uint8_t *d_valid, float *d_out, uint8_t *d_status,
+                                    bto_stream stream);
+
+/* Pathline stitching (Sec. 3.2): new particles follow the basis flows of
+ * successive intervals. In interval k a particle's next position is the
+ * trilinear interpolant (Eq. 1 per axis; the lattice stand-in for the
+ * paper's barycentric interpolation) of the end positions of the 8 basis
+ * flows of its seed-lattice cell. Outside the lattice, or in a cell with a
+ * missing (NaN) basis flow, the particle stops and its later positions are
+ * NaN.
+ *   lattice[3], origin[3], spacing[3]  seed lattice (host): point j at
+ *                origin + j * spacing, j = 0..lattice-1 per axis
+ *   d_ends_table DEVICE array of `intervals` device pointers, each P*3 floats
+ *                of lattice end positions in canonical order (bto_fill_lattice
+ *                output)
+ *   d_start      nq*3 floats, start positions (physical)
+ *   d_path       (intervals+1)*nq*3 floats written: positions at the start
+ *                and at the end of every interval */
+BTO_API bto_status bto_stitch_pathlines(const int32_t lattice[3], const float origin[3],
+                                        const float spacing[3], int32_t intervals,
+                                        const float *const *d_ends_table, int64_t nq,
+                                        const float *d_start, float *d_path, bto_stream stream);
 
 /* ---- Adjoint: gradients of a loss on end positions ----------------------
  *

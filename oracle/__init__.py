@@ -70,7 +70,7 @@ def _load():
     lib.bto_oracle_sample.argtypes = [fp, i64p, dp, dp, ctypes.c_int64, dp, dp]
     lib.bto_oracle_sample.restype = None
     lib.bto_oracle_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int32,
-                                     ctypes.c_int64, dp, i32p, dp, ctypes.c_int32]
+                                     ctypes.c_int64, dp, i32p, dp, dp, dp, ctypes.c_int32]
     lib.bto_oracle_cycle.restype = None
     u8p = ctypes.POINTER(ctypes.c_uint8)
     lib.bto_oracle_adjoint_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int64, dp, u8p, dp,
@@ -173,6 +173,8 @@ class State:
         m = self.x.shape[0]
         self.exit_cycle = np.full(m, -1, dtype=np.int32)
         self.min_margin = np.full(m, np.inf, dtype=np.float64)
+        self.exit_pos = np.full((m, 3), np.nan, dtype=np.float64)
+        self.exit_time = np.full(m, np.nan, dtype=np.float64)
 
     @property
     def valid(self) -> np.ndarray:
@@ -190,7 +192,9 @@ def cycle(grid: Grid, field: np.ndarray, dt: float, c: int, state: State,
                          float(dt), int(c), state.x.shape[0],
                          _ptr(state.x, ctypes.c_double),
                          _ptr(state.exit_cycle, ctypes.c_int32),
-                         _ptr(state.min_margin, ctypes.c_double), int(nthreads))
+                         _ptr(state.min_margin, ctypes.c_double),
+                         _ptr(state.exit_pos, ctypes.c_double), _ptr(state.exit_time, ctypes.c_double),
+                         int(nthreads))
 
 
 def run_interval(grid: Grid, stride: int, cycles: int, dt: float, field_of_cycle,
@@ -261,6 +265,87 @@ def vjp(grid: Grid, field_of_cycle, dt: float, x0: np.ndarray, cycles: int, grad
         adjoint_cycle(grid, field_of_cycle(c), dt, xs[c], alive, lam, g)
         gF[c] = g
     return st, lam, gF
+
+
+# ---------------------------------------------------------------------------
+# Post hoc reconstruction of missing basis flows (Sec. 3.2; Eq. 2)
+# ---------------------------------------------------------------------------
+def fill_lattice(S, ends: np.ndarray, valid: np.ndarray):
+    """Lattice stand-in for the paper's neighbourhood reconstruction: each
+    missing entry J takes, along the axis whose nearest valid neighbours on
+    both sides are closest (ties x, y, z), the linear interpolant of Eq. (1)
+    between them at J. Returns (filled ends, status: 1 valid, 2 filled,
+    0 missing). Plain loops, test sizes only."""
+    Sx, Sy, Sz = (int(v) for v in S)
+    E = np.asarray(ends, dtype=np.float64).reshape(Sz, Sy, Sx, 3)
+    V = np.asarray(valid).reshape(Sz, Sy, Sx).astype(bool)
+    out = np.full_like(E, np.nan)
+    status = np.zeros((Sz, Sy, Sx), dtype=np.uint8)
+    out[V] = E[V]
+    status[V] = 1
+    dims = (Sx, Sy, Sz)
+    for jz, jy, jx in zip(*np.nonzero(~V)):
+        j = [jx, jy, jz]
+        best = None
+        for ax in range(3):
+            def at(off):
+                jj = list(j)
+                jj[ax] += off
+                return jj
+            a = 1
+            while j[ax] - a >= 0 and not V[tuple(reversed(at(-a)))]:
+                a += 1
+            if j[ax] - a < 0:
+                continue
+            b = 1
+            while j[ax] + b < dims[ax] and not V[tuple(reversed(at(b)))]:
+                b += 1
+            if j[ax] + b >= dims[ax]:
+                continue
+            if best is None or a + b < best[1] + best[2]:
+                best = (ax, a, b, at(-a), at(b))
+        if best is None:
+            continue
+        ax, a, b, jl, jr = best
+        x0, x1, x = -a, b, 0.0
+        fl, fr = E[tuple(reversed(jl))], E[tuple(reversed(jr))]
+        # Eq. (1): L(x) = (x - x0)/(x1 - x0) f(x1) + (x1 - x)/(x1 - x0) f(x0)
+        out[jz, jy, jx] = (x - x0) / (x1 - x0) * fr + (x1 - x) / (x1 - x0) * fl
+        status[jz, jy, jx] = 2
+    return out.reshape(-1, 3), status.reshape(-1)
+
+
+def stitch(S, origin, spacing, ends_list, start):
+    """Pathline stitching (Sec. 3.2) on a seed lattice: in interval k the next
+    position is the trilinear interpolant (Eq. 1 per axis) of the end
+    positions of the 8 basis flows of the particle's lattice cell. Outside
+    the lattice or next to a missing (NaN) entry the particle stops (NaN).
+    Returns (intervals + 1, nq, 3)."""
+    S = [int(v) for v in S]
+    o = np.asarray(origin, dtype=np.float32).astype(np.float64)
+    sp = np.asarray(spacing, dtype=np.float32).astype(np.float64)
+    x = np.asarray(start, dtype=np.float64).reshape(-1, 3).copy()
+    path = [x.copy()]
+    for E in ends_list:
+        E = np.asarray(E, dtype=np.float64).reshape(S[2], S[1], S[0], 3)
+        nxt = np.full_like(x, np.nan)
+        for i in range(x.shape[0]):
+            u = (x[i] - o) / sp
+            if not np.all(np.isfinite(u)) or np.any(u < 0) or np.any(u > np.array(S) - 1):
+                continue
+            cell = [min(int(np.floor(u[a])), max(S[a] - 2, 0)) for a in range(3)]
+            t = [u[a] - cell[a] for a in range(3)]
+            acc = np.zeros(3)
+            for c in range(2):
+                for b in range(2):
+                    for a in range(2):
+                        w = (t[0] if a else 1 - t[0]) * (t[1] if b else 1 - t[1]) * (t[2] if c else 1 - t[2])
+                        j = [min(cell[0] + a, S[0] - 1), min(cell[1] + b, S[1] - 1), min(cell[2] + c, S[2] - 1)]
+                        acc += w * E[j[2], j[1], j[0]]
+            nxt[i] = acc
+        x = nxt
+        path.append(x.copy())
+    return np.stack(path)
 
 
 # ---------------------------------------------------------------------------

@@ -155,17 +155,50 @@ static double margin_cells(const int64_t n[3], const double origin[3],
  *   p3 = x + dt/2 k2   -> tested, k3 = v(p3)
  *   p4 = x + dt   k3   -> tested, k4 = v(p4)
  *   x' = x + dt/6 (k1 + 2 k2 + 2 k3 + k4) -> tested
- * On the first failing test: exit_cycle = cycle, x unchanged.
+ * On the first failing test: exit_cycle = cycle, x unchanged, and (when the
+ * arrays are given) exit_pos / exit_time receive the clipped exit location.
  * min_margin[p] keeps the smallest |margin| (cells) over the tested points,
  * which the parity check uses for its near-face exemption.
  * x: m*3 doubles (in/out); exit_cycle: m ints, -1 while alive (in/out);
  * min_margin: m doubles (in/out), start at +inf.
+ * exit_pos: m*3 doubles or NULL; exit_time: m doubles or NULL (outputs).
  * ------------------------------------------------------------------------- */
+/* Termination location (storing it is the paper's future work, Sec. 6;
+ * reading of this library): the chord from the last in-block position x to
+ * the first tested point q found outside is clipped to the closed box,
+ * t = largest value in [0, 1] with x + t (q - x) inside; the exit time is
+ * cycle + t * f, f = 1/2 when q was p2 or p3, 1 for p4 or the end point. A q
+ * with a NaN component gives no direction: location x, t = 0. */
+static void clip_exit(const int64_t n[3], const double origin[3], const double h[3],
+                      const double x[3], const double q[3], double f, int32_t cycle,
+                      double *pos, double *time)
+{
+    if (isnan(q[0]) || isnan(q[1]) || isnan(q[2])) {
+        for (int a = 0; a < 3; ++a) pos[a] = x[a];
+        *time = (double)cycle;
+        return;
+    }
+    double t = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double xi = (x[a] - origin[a]) / h[a], qi = (q[a] - origin[a]) / h[a];
+        if (qi > (double)n[a]) { double ta = ((double)n[a] - xi) / (qi - xi); if (ta < t) t = ta; }
+        if (qi < 0.0) { double ta = (0.0 - xi) / (qi - xi); if (ta < t) t = ta; }
+    }
+    if (t < 0.0) t = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double lo = origin[a], hi = origin[a] + (double)n[a] * h[a];
+        double v = x[a] + t * (q[a] - x[a]);
+        pos[a] = v < lo ? lo : (v > hi ? hi : v);
+    }
+    *time = (double)cycle + t * f;
+}
+
 ORACLE_API void bto_oracle_cycle(const float *field, const int64_t n[3],
                                  const double origin[3], const double h[3],
                                  double dt, int32_t cycle, int64_t m,
                                  double *x, int32_t *exit_cycle,
-                                 double *min_margin, int32_t nthreads)
+                                 double *min_margin, double *exit_pos, double *exit_time,
+                                 int32_t nthreads)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -176,6 +209,7 @@ ORACLE_API void bto_oracle_cycle(const float *field, const int64_t n[3],
         double *xp = x + 3 * p;
         double k1[3], k2[3], k3[3], k4[3], q[3];
         double mm = min_margin[p];
+        double f = 0.0;
         int in;
         double d;
 
@@ -184,28 +218,33 @@ ORACLE_API void bto_oracle_cycle(const float *field, const int64_t n[3],
         for (int a = 0; a < 3; ++a) q[a] = xp[a] + 0.5 * dt * k1[a];
         d = margin_cells(n, origin, h, q, &in);
         if (fabs(d) < mm) mm = fabs(d);
-        if (!in) { exit_cycle[p] = cycle; min_margin[p] = mm; continue; }
+        if (!in) { f = 0.5; goto terminated; }
         sample(field, n, origin, h, q, k2);
 
         for (int a = 0; a < 3; ++a) q[a] = xp[a] + 0.5 * dt * k2[a];
         d = margin_cells(n, origin, h, q, &in);
         if (fabs(d) < mm) mm = fabs(d);
-        if (!in) { exit_cycle[p] = cycle; min_margin[p] = mm; continue; }
+        if (!in) { f = 0.5; goto terminated; }
         sample(field, n, origin, h, q, k3);
 
         for (int a = 0; a < 3; ++a) q[a] = xp[a] + dt * k3[a];
         d = margin_cells(n, origin, h, q, &in);
         if (fabs(d) < mm) mm = fabs(d);
-        if (!in) { exit_cycle[p] = cycle; min_margin[p] = mm; continue; }
+        if (!in) { f = 1.0; goto terminated; }
         sample(field, n, origin, h, q, k4);
 
         for (int a = 0; a < 3; ++a)
             q[a] = xp[a] + dt / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
         d = margin_cells(n, origin, h, q, &in);
         if (fabs(d) < mm) mm = fabs(d);
+        if (!in) { f = 1.0; goto terminated; }
         min_margin[p] = mm;
-        if (!in) { exit_cycle[p] = cycle; continue; }
         for (int a = 0; a < 3; ++a) xp[a] = q[a];
+        continue;
+    terminated:
+        min_margin[p] = mm;
+        exit_cycle[p] = cycle;
+        if (exit_pos && exit_time) clip_exit(n, origin, h, xp, q, f, cycle, exit_pos + 3 * p, exit_time + p);
     }
 }
 

@@ -55,6 +55,7 @@ def _declare(lib):
         "bto_advect_cycle": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_batch_advect_cycle": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_end_interval": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "bto_end_interval_ex": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_launch_interval_graph": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
@@ -65,6 +66,9 @@ def _declare(lib):
         "bto_interval_noalloc": ([c_i32p, c_fp, c_fp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_float,
                                   vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_destroy": ([vp], None),
+        "bto_fill_lattice": ([c_i32p, vp, vp, vp, vp, vp], ctypes.c_int),
+        "bto_stitch_pathlines": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp],
+                                 ctypes.c_int),
         "bto_tape_create": ([c_i32p, c_fp, c_fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                              ctypes.POINTER(vp)], ctypes.c_int),
         "bto_tape_num_particles": ([vp], ctypes.c_int64),
@@ -189,6 +193,13 @@ def bto_end_interval(ctx: int, d_seeds, d_ends, d_valid, d_exit_cycle=None, stre
                                    _addr(d_exit_cycle), _stream(stream)), "bto_end_interval")
 
 
+def bto_end_interval_ex(ctx: int, d_seeds, d_ends, d_valid, d_exit_cycle=None, d_exit_pos=None,
+                        d_exit_time=None, stream=None) -> None:
+    _check(load().bto_end_interval_ex(ctx, _addr(d_seeds), _addr(d_ends), _addr(d_valid), _addr(d_exit_cycle),
+                                      _addr(d_exit_pos), _addr(d_exit_time), _stream(stream)),
+           "bto_end_interval_ex")
+
+
 def bto_launch_interval_graph(ctx: int, d_field_table, dt: float, stream=None) -> None:
     _check(load().bto_launch_interval_graph(ctx, _addr(d_field_table), float(dt), _stream(stream)),
            "bto_launch_interval_graph")
@@ -242,6 +253,18 @@ def bto_interval_noalloc(extent_cells, origin, spacing, seed_stride: int, interv
                                        _addr(d_field_table), float(dt), _addr(d_seeds), _addr(d_ends),
                                        _addr(d_valid), _addr(d_exit_cycle), _stream(stream)),
            "bto_interval_noalloc")
+
+
+def bto_fill_lattice(lattice, d_ends, d_valid, d_out, d_status=None, stream=None) -> None:
+    _check(load().bto_fill_lattice(_arr(ctypes.c_int32, lattice), _addr(d_ends), _addr(d_valid), _addr(d_out),
+                                   _addr(d_status), _stream(stream)), "bto_fill_lattice")
+
+
+def bto_stitch_pathlines(lattice, origin, spacing, intervals: int, d_ends_table, nq: int, d_start, d_path,
+                         stream=None) -> None:
+    _check(load().bto_stitch_pathlines(_arr(ctypes.c_int32, lattice), _arr(ctypes.c_float, origin),
+                                       _arr(ctypes.c_float, spacing), int(intervals), _addr(d_ends_table), int(nq),
+                                       _addr(d_start), _addr(d_path), _stream(stream)), "bto_stitch_pathlines")
 
 
 def bto_tape_create(extent_cells, origin, spacing, num_particles: int, cycles: int,
@@ -340,10 +363,20 @@ class Context:
                 "valid": torch.empty((self.P,), dtype=torch.uint8, device=dev),
                 "exit_cycle": torch.empty((self.P,), dtype=torch.int32, device=dev)}
 
-    def end_interval(self, out=None, stream=None):
+    def end_interval(self, out=None, stream=None, exits=False):
+        """Basis flows of the interval (dict of tensors); with exits=True also
+        the clipped termination locations and times."""
         out = out if out is not None else self.alloc_outputs()
-        bto_end_interval(self.handle, out["seeds"], out["ends"], out["valid"],
-                         out.get("exit_cycle"), stream)
+        if exits:
+            import torch
+            dev = out["seeds"].device
+            out.setdefault("exit_pos", torch.empty((self.P, 3), dtype=torch.float32, device=dev))
+            out.setdefault("exit_time", torch.empty((self.P,), dtype=torch.float32, device=dev))
+            bto_end_interval_ex(self.handle, out["seeds"], out["ends"], out["valid"], out.get("exit_cycle"),
+                                out["exit_pos"], out["exit_time"], stream)
+        else:
+            bto_end_interval(self.handle, out["seeds"], out["ends"], out["valid"],
+                             out.get("exit_cycle"), stream)
         return out
 
     def autotune(self, field_table, cycles, dt, stream=None):

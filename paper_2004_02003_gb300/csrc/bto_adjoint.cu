@@ -138,8 +138,8 @@ __global__ void tape_step_kernel(const BlockDev *__restrict__ blk, const void *c
         float4 r = in[i];
         const int32_t e = exitc[i];
         if (alive_at(e, c)) {
-            float3 x = make_float3(r.x, r.y, r.z);
-            if (rk4_step<bto::LAYOUT_F3>(x, field, g, s)) {
+            float3 x = make_float3(r.x, r.y, r.z), q;
+            if (rk4_step<bto::LAYOUT_F3>(x, field, g, s, q) == 0) {
                 r.x = x.x; r.y = x.y; r.z = x.z;
             } else if (record) {
                 exitc[i] = c;

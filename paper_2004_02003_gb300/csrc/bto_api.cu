@@ -43,6 +43,7 @@ struct bto_ctx {
     float4 *act[2] = {nullptr, nullptr};
     int32_t *gcnt[2] = {nullptr, nullptr};
     float4 *term = nullptr;
+    float4 *clip = nullptr;        // [P] clipped exit location (xi) and time per canonical id
     int64_t *diag_dst = nullptr;   // bto_copy_active scratch
     bto_status sticky = BTO_OK;
     // cached interval graph
@@ -119,6 +120,7 @@ void free_ctx(bto_ctx *c) {
     cudaFree(c->gcnt[0]);
     cudaFree(c->gcnt[1]);
     cudaFree(c->term);
+    cudaFree(c->clip);
     cudaFree(c->diag_dst);
     cudaFree(c->f4buf[0]);
     cudaFree(c->f4buf[1]);
@@ -234,6 +236,7 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[0], sizeof(int32_t) * units);
     if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[1], sizeof(int32_t) * units);
     if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->clip, sizeof(float4) * (size_t)P);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->blocks, bl.data(), sizeof(BlockDev) * (size_t)nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -273,7 +276,7 @@ bto_status advect_ingest(bto_ctx *c, const void *field, const void *const *field
         BTO_CUDA(cudaEventRecord(c->ing_done[k], c->side));
         BTO_CUDA(cudaStreamWaitEvent(s, c->ing_done[k], 0));
         const int64_t region = (b + 1 < c->nb ? c->blocks_h[(size_t)b + 1].slot_base : c->slots) - B.slot_base;
-        bto::AdvectArgs a;
+        bto::AdvectArgs a{};
         a.blocks = c->blocks + b;
         a.gblock = c->gblock;
         a.nb = 1;
@@ -286,6 +289,7 @@ bto_status advect_ingest(bto_ctx *c, const void *field, const void *const *field
         a.gcnt_out = c->gcnt[(cyc + 1) & 1] + B.slot_base / G;
         a.ngroups = region / G;
         a.term = c->term;
+        a.clip = c->clip;
         a.dt = dt;
         const int64_t need = (a.ngroups + c->nt / 32 - 1) / (c->nt / 32);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->grid, need));
@@ -307,7 +311,7 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     if (c->cycle >= c->L) return BTO_ERR_STATE;
     if (c->ingest) return advect_ingest(c, field, fields, dt, s);
     const int cyc = c->cycle;
-    bto::AdvectArgs a;
+    bto::AdvectArgs a{};
     a.blocks = c->blocks;
     a.gblock = c->gblock;
     a.nb = c->nb;
@@ -320,6 +324,7 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     a.gcnt_out = c->gcnt[(cyc + 1) & 1];
     a.ngroups = c->slots / group_size(c);
     a.term = c->term;
+    a.clip = c->clip;
     a.dt = dt;
     cudaError_t e = bto::launch_advect(a, c->layout, c->nt, c->ppt, c->cap, c->grid, c->dyn_smem, s);
     if (e != cudaSuccess) {
@@ -455,11 +460,13 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
     return BTO_OK;
 }
 
-bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t *d_valid,
-                            int32_t *d_exit_cycle, bto_stream stream) {
+bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t *d_valid,
+                               int32_t *d_exit_cycle, float *d_exit_pos, float *d_exit_time,
+                               bto_stream stream) {
     if (!ctx || !d_seeds || !d_ends || !d_valid) return BTO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_seeds) % 4 || reinterpret_cast<uintptr_t>(d_ends) % 4 ||
-        reinterpret_cast<uintptr_t>(d_exit_cycle) % 4)
+        reinterpret_cast<uintptr_t>(d_exit_cycle) % 4 || reinterpret_cast<uintptr_t>(d_exit_pos) % 4 ||
+        reinterpret_cast<uintptr_t>(d_exit_time) % 4)
         return BTO_ERR_INVALID_ARG;
     if (ctx->cycle != ctx->L) return BTO_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -469,8 +476,13 @@ bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t
                                     ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
                                     grid, s));
     BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
-                                    d_valid, d_exit_cycle, grid, s));
+                                    d_valid, d_exit_cycle, grid, s, ctx->clip, d_exit_pos, d_exit_time));
     return seed(ctx, s);
+}
+
+bto_status bto_end_interval(bto_ctx *ctx, float *d_seeds, float *d_ends, uint8_t *d_valid,
+                            int32_t *d_exit_cycle, bto_stream stream) {
+    return bto_end_interval_ex(ctx, d_seeds, d_ends, d_valid, d_exit_cycle, nullptr, nullptr, stream);
 }
 
 bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta, int32_t particles_per_thread,
@@ -611,6 +623,41 @@ bto_status bto_last_error(bto_ctx *ctx) {
     if (st == BTO_OK && e != cudaSuccess) st = cuda_status(e);
     ctx->sticky = BTO_OK;
     return st;
+}
+
+bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_ends, const uint8_t *d_valid,
+                            float *d_out, uint8_t *d_status, bto_stream stream) {
+    if (!lattice || !d_ends || !d_valid || !d_out) return BTO_ERR_INVALID_ARG;
+    if (lattice[0] < 1 || lattice[1] < 1 || lattice[2] < 1) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_ends) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
+        return BTO_ERR_INVALID_ARG;
+    const int64_t P = (int64_t)lattice[0] * lattice[1] * lattice[2];
+    if (P > (1ll << 31) - 1) return BTO_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    BTO_CUDA(cudaGetDevice(&dev));
+    BTO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, (int64_t)sms * 8));
+    BTO_CUDA(bto::launch_fill_lattice(lattice, d_ends, d_valid, d_out, d_status, grid, (cudaStream_t)stream));
+    return BTO_OK;
+}
+
+bto_status bto_stitch_pathlines(const int32_t lattice[3], const float origin[3], const float spacing[3],
+                                int32_t intervals, const float *const *d_ends_table, int64_t nq,
+                                const float *d_start, float *d_path, bto_stream stream) {
+    if (!lattice || !origin || !spacing || !d_ends_table || !d_start || !d_path) return BTO_ERR_INVALID_ARG;
+    if (intervals < 1 || nq < 1) return BTO_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (lattice[a] < 1 || !std::isfinite(origin[a]) || !finite_pos(spacing[a])) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_ends_table) % alignof(void *) || reinterpret_cast<uintptr_t>(d_start) % 4 ||
+        reinterpret_cast<uintptr_t>(d_path) % 4)
+        return BTO_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    BTO_CUDA(cudaGetDevice(&dev));
+    BTO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8));
+    BTO_CUDA(bto::launch_stitch(lattice, origin, spacing, intervals, d_ends_table, nq, d_start, d_path, grid,
+                                (cudaStream_t)stream));
+    return BTO_OK;
 }
 
 const char *bto_status_string(bto_status s) {

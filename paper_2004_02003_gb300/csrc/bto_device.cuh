@@ -102,32 +102,56 @@ __device__ __forceinline__ float3 sample(Cell &C, const void *__restrict__ field
     return trilerp(C.v, x - (float)ix, y - (float)iy, z - (float)iz);
 }
 
-// One RK4 step in cell units (s = dt / h per axis). Returns false, leaving x
-// unchanged, as soon as a stage point or the end point leaves the block.
+// One RK4 step in cell units (s = dt / h per axis). Returns 0 and moves x
+// when every tested point stays in the block; otherwise returns the stage
+// whose point left first (1 = p2, 2 = p3, 3 = p4, 4 = end point), leaves x
+// unchanged and stores that point in q.
 template <int LAYOUT>
-__device__ __forceinline__ bool rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
-                                         const float3 s) {
+__device__ __forceinline__ int rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
+                                        const float3 s, float3 &q) {
     const float3 hs = make_float3(0.5f * s.x, 0.5f * s.y, 0.5f * s.z);
     Cell C;
     C.ix = -1; C.iy = -1; C.iz = -1;
     const float3 k1 = sample<LAYOUT>(C, field, g, x.x, x.y, x.z);
     float px = fmaf(hs.x, k1.x, x.x), py = fmaf(hs.y, k1.y, x.y), pz = fmaf(hs.z, k1.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
+    if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 1; }
     const float3 k2 = sample<LAYOUT>(C, field, g, px, py, pz);
     float3 acc = make_float3(k1.x + 2.f * k2.x, k1.y + 2.f * k2.y, k1.z + 2.f * k2.z);
     px = fmaf(hs.x, k2.x, x.x); py = fmaf(hs.y, k2.y, x.y); pz = fmaf(hs.z, k2.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
+    if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 2; }
     const float3 k3 = sample<LAYOUT>(C, field, g, px, py, pz);
     acc.x = fmaf(2.f, k3.x, acc.x); acc.y = fmaf(2.f, k3.y, acc.y); acc.z = fmaf(2.f, k3.z, acc.z);
     px = fmaf(s.x, k3.x, x.x); py = fmaf(s.y, k3.y, x.y); pz = fmaf(s.z, k3.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
+    if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 3; }
     const float3 k4 = sample<LAYOUT>(C, field, g, px, py, pz);
     acc.x += k4.x; acc.y += k4.y; acc.z += k4.z;
     const float sx6 = s.x * (1.f / 6.f), sy6 = s.y * (1.f / 6.f), sz6 = s.z * (1.f / 6.f);
     px = fmaf(sx6, acc.x, x.x); py = fmaf(sy6, acc.y, x.y); pz = fmaf(sz6, acc.z, x.z);
-    if (!inside(g, px, py, pz)) return false;
+    if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 4; }
     x = make_float3(px, py, pz);
-    return true;
+    return 0;
+}
+
+// Termination location (the paper's future work, Sec. 6): the chord from the
+// last in-block position x to the first point q found outside is clipped to
+// the block, t = largest value in [0, 1] with x + t (q - x) inside; the exit
+// time is the cycle plus t times the fraction of the step at which q was
+// taken (1/2 for p2 and p3, 1 for p4 and the end point). A q with a NaN
+// component gives no direction: the location is x and t = 0.
+__device__ __forceinline__ float4 clip_exit(const Geo &g, float3 x, float3 q, int stage, int cycle) {
+    if (!(q.x == q.x && q.y == q.y && q.z == q.z)) return make_float4(x.x, x.y, x.z, (float)cycle);
+    float t = 1.f;
+    const float xs[3] = {x.x, x.y, x.z}, qs[3] = {q.x, q.y, q.z}, ns[3] = {g.fnx, g.fny, g.fnz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (qs[a] > ns[a]) t = fminf(t, (ns[a] - xs[a]) / (qs[a] - xs[a]));
+        if (qs[a] < 0.f) t = fminf(t, (0.f - xs[a]) / (qs[a] - xs[a]));
+    }
+    t = fmaxf(t, 0.f);
+    const float cx = fminf(fmaxf(fmaf(t, q.x - x.x, x.x), 0.f), g.fnx);
+    const float cy = fminf(fmaxf(fmaf(t, q.y - x.y, x.y), 0.f), g.fny);
+    const float cz = fminf(fmaxf(fmaf(t, q.z - x.z, x.z), 0.f), g.fnz);
+    return make_float4(cx, cy, cz, (float)cycle + t * (stage <= 2 ? 0.5f : 1.f));
 }
 
 

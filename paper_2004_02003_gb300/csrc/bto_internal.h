@@ -46,6 +46,7 @@ struct AdvectArgs {
     int32_t *gcnt_out;           // [ngroups] survivors per group
     int64_t ngroups;
     float4 *term;                // [P] termination record per canonical id
+    float4 *clip;                // [P] clipped exit location (xi) and time, or NULL
     float dt;
 };
 
@@ -66,8 +67,14 @@ cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int
                                int64_t slots, int group, float4 *out, int grid, cudaStream_t s);
 cudaError_t launch_ingest(const void *field, const void *const *fields, int b, int64_t nodes, float4 *out,
                           int grid, cudaStream_t s);
+cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
+                          const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,
+                          cudaStream_t s);
+cudaError_t launch_fill_lattice(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
+                                uint8_t *status, int grid, cudaStream_t s);
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,
                               float *seeds, float *ends, uint8_t *valid, int32_t *exit_cycle,
-                              int grid, cudaStream_t s);
+                              int grid, cudaStream_t s, const float4 *clip = nullptr,
+                              float *exit_pos = nullptr, float *exit_time = nullptr);
 
 }  // namespace bto

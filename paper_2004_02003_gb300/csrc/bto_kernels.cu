@@ -92,13 +92,15 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
             const int i = k * 32 + lane;
             bool surv = false;
             if (i < cnt) {
-                float3 x = make_float3(r[k].x, r[k].y, r[k].z);
-                surv = rk4_step<LAYOUT>(x, field, g, s);
+                float3 x = make_float3(r[k].x, r[k].y, r[k].z), q;
+                const int failed = rk4_step<LAYOUT>(x, field, g, s, q);
+                surv = failed == 0;
                 if (surv) {
                     r[k].x = x.x; r[k].y = x.y; r[k].z = x.z;
                 } else {
-                    __stcs(a.term + idbase + __float_as_int(r[k].w),
-                           make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
+                    const int64_t gid = idbase + __float_as_int(r[k].w);
+                    __stcs(a.term + gid, make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
+                    if (a.clip) __stcs(a.clip + gid, clip_exit(g, x, q, failed, a.cycle));
                 }
             }
             const unsigned m = __ballot_sync(kFull, surv);
@@ -155,12 +157,14 @@ __global__ void write_live_kernel(const BlockDev *__restrict__ blocks,
     }
 }
 
-// K4b: seeds of every particle, plus end/valid/exit of the terminated ones;
-// clears the termination record for the next interval.
+// K4b: seeds of every particle, plus end/valid/exit of the terminated ones
+// (and, when asked, their clipped exit location and time); clears the
+// termination record for the next interval.
 __global__ void write_term_kernel(const BlockDev *__restrict__ blocks, int32_t nb, int64_t P,
                                   float4 *__restrict__ term, float *__restrict__ seeds,
                                   float *__restrict__ ends, uint8_t *__restrict__ valid,
-                                  int32_t *__restrict__ exit_cycle) {
+                                  int32_t *__restrict__ exit_cycle, const float4 *__restrict__ clip,
+                                  float *__restrict__ exit_pos, float *__restrict__ exit_time) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < P; gid += stride) {
         const int b = nb == 1 ? 0 : find_block(blocks, nb, gid);
@@ -184,7 +188,24 @@ __global__ void write_term_kernel(const BlockDev *__restrict__ blocks, int32_t n
             }
             if (valid) valid[gid] = 0;
             if (exit_cycle) exit_cycle[gid] = e;
+            if (clip && (exit_pos || exit_time)) {
+                const float4 cl = clip[gid];
+                if (exit_pos) {
+                    exit_pos[3 * gid + 0] = fmaf(cl.x, B.h[0], B.origin[0]);
+                    exit_pos[3 * gid + 1] = fmaf(cl.y, B.h[1], B.origin[1]);
+                    exit_pos[3 * gid + 2] = fmaf(cl.z, B.h[2], B.origin[2]);
+                }
+                if (exit_time) exit_time[gid] = cl.w;
+            }
             term[gid] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        } else if (exit_pos || exit_time) {
+            const float nan = __int_as_float(0x7fc00000);
+            if (exit_pos) {
+                exit_pos[3 * gid + 0] = nan;
+                exit_pos[3 * gid + 1] = nan;
+                exit_pos[3 * gid + 2] = nan;
+            }
+            if (exit_time) exit_time[gid] = nan;
         }
     }
 }
@@ -228,6 +249,98 @@ __global__ void ingest_f3_f4_kernel(const void *__restrict__ field, const void *
     }
     for (int64_t i = quads * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += stride)
         out[i] = make_float4(__ldcs(f + 3 * i), __ldcs(f + 3 * i + 1), __ldcs(f + 3 * i + 2), 0.f);
+}
+
+// Post hoc lattice reconstruction (Sec. 3.2 / Sec. 3.3, Eq. 2): a missing
+// basis flow at lattice point J takes, along the axis whose nearest valid
+// neighbours on both sides are closest (a + b smallest; ties x, y, z), the
+// linear interpolant (Eq. 1) of their end positions at J:
+//   end(J) = (b end(J - a e) + a end(J + b e)) / (a + b).
+// Eq. (2): interpolating from the filled value afterwards equals
+// interpolating from the two neighbours directly. Entries with no axis
+// holding valid neighbours on both sides stay missing.
+__global__ void fill_lattice_kernel(int3 S, const float *__restrict__ ends, const uint8_t *__restrict__ valid,
+                                    float *__restrict__ out, uint8_t *__restrict__ status) {
+    const int64_t P = (int64_t)S.x * S.y * S.z;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+        if (valid[p]) {
+            out[3 * p] = ends[3 * p]; out[3 * p + 1] = ends[3 * p + 1]; out[3 * p + 2] = ends[3 * p + 2];
+            if (status) status[p] = 1;
+            continue;
+        }
+        const int jx = (int)(p % S.x), jy = (int)((p / S.x) % S.y), jz = (int)(p / ((int64_t)S.x * S.y));
+        const int j[3] = {jx, jy, jz};
+        const int ext[3] = {S.x, S.y, S.z};
+        const int64_t step[3] = {1, S.x, (int64_t)S.x * S.y};
+        int best_axis = -1, best_a = 0, best_b = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            int a = 1;
+            while (j[ax] - a >= 0 && !valid[p - a * step[ax]]) ++a;
+            if (j[ax] - a < 0) continue;
+            int b = 1;
+            while (j[ax] + b < ext[ax] && !valid[p + b * step[ax]]) ++b;
+            if (j[ax] + b >= ext[ax]) continue;
+            if (best_axis < 0 || a + b < best_a + best_b) { best_axis = ax; best_a = a; best_b = b; }
+        }
+        if (best_axis < 0) {
+            const float nan = __int_as_float(0x7fc00000);
+            out[3 * p] = nan; out[3 * p + 1] = nan; out[3 * p + 2] = nan;
+            if (status) status[p] = 0;
+            continue;
+        }
+        const int64_t pl = p - best_a * step[best_axis], pr = p + best_b * step[best_axis];
+        const float wl = (float)best_b / (float)(best_a + best_b), wr = (float)best_a / (float)(best_a + best_b);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[3 * p + k] = wl * ends[3 * pl + k] + wr * ends[3 * pr + k];
+        if (status) status[p] = 2;
+    }
+}
+
+// Pathline stitching (Sec. 3.2): a new particle follows the basis flows of
+// successive intervals. At the start of interval k it sits in a cell of the
+// seed lattice; its position at the end of the interval is the trilinear
+// interpolant (Eq. 1 per axis) of the end positions of that cell's 8 basis
+// flows. A particle outside the lattice, or whose cell has a missing basis
+// flow (NaN), stops: its later positions are NaN.
+__global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t intervals,
+                              const float *const *__restrict__ ends_table, int64_t nq,
+                              const float *__restrict__ start, float *__restrict__ path) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float nan = __int_as_float(0x7fc00000);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += stride) {
+        float x = start[3 * i], y = start[3 * i + 1], z = start[3 * i + 2];
+        path[3 * i] = x; path[3 * i + 1] = y; path[3 * i + 2] = z;
+        for (int32_t k = 0; k < intervals; ++k) {
+            float nx = nan, ny = nan, nz = nan;
+            const float u = (x - origin.x) * inv_sp.x, v = (y - origin.y) * inv_sp.y, w = (z - origin.z) * inv_sp.z;
+            const bool in = u >= 0.f && v >= 0.f && w >= 0.f && u <= (float)(S.x - 1) &&
+                            v <= (float)(S.y - 1) && w <= (float)(S.z - 1);
+            if (in) {
+                const int ix = min((int)u, max(S.x - 2, 0)), iy = min((int)v, max(S.y - 2, 0)),
+                          iz = min((int)w, max(S.z - 2, 0));
+                const float fx = u - ix, fy = v - iy, fz = w - iz;
+                const float *E = ends_table[k];
+                float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            const int jx = min(ix + a, S.x - 1), jy = min(iy + b, S.y - 1), jz = min(iz + c, S.z - 1);
+                            const float wgt = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (c ? fz : 1.f - fz);
+                            const int64_t p = jx + (int64_t)S.x * (jy + (int64_t)S.y * jz);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
+                        }
+                nx = acc[0]; ny = acc[1]; nz = acc[2];
+            }
+            x = nx; y = ny; z = nz;
+            const int64_t o = 3 * ((int64_t)(k + 1) * nq + i);
+            path[o] = x; path[o + 1] = y; path[o + 2] = z;
+        }
+    }
 }
 
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
@@ -305,10 +418,27 @@ cudaError_t launch_ingest(const void *field, const void *const *fields, int b, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
+                          const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,
+                          cudaStream_t s) {
+    stitch_kernel<<<grid, 256, 0, s>>>(make_int3(S[0], S[1], S[2]), make_float3(origin[0], origin[1], origin[2]),
+                                       make_float3(1.f / spacing[0], 1.f / spacing[1], 1.f / spacing[2]),
+                                       intervals, ends_table, nq, start, path);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_lattice(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
+                                uint8_t *status, int grid, cudaStream_t s) {
+    fill_lattice_kernel<<<grid, 256, 0, s>>>(make_int3(S[0], S[1], S[2]), ends, valid, out, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,
                               float *seeds, float *ends, uint8_t *valid, int32_t *exit_cycle,
-                              int grid, cudaStream_t s) {
-    write_term_kernel<<<grid, 256, 0, s>>>(blocks, nb, P, term, seeds, ends, valid, exit_cycle);
+                              int grid, cudaStream_t s, const float4 *clip, float *exit_pos,
+                              float *exit_time) {
+    write_term_kernel<<<grid, 256, 0, s>>>(blocks, nb, P, term, seeds, ends, valid, exit_cycle, clip,
+                                           exit_pos, exit_time);
     return cudaGetLastError();
 }
 

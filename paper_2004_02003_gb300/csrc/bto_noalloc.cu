@@ -160,7 +160,7 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
     e = cudaGetLastError();
     if (e == cudaSuccess) e = bto::launch_seed(blk, gblock, perm, slots, group, act[0], gcnt[0], aux, s);
     for (int32_t c = 0; c < interval_cycles && e == cudaSuccess; ++c) {
-        bto::AdvectArgs a;
+        bto::AdvectArgs a{};
         a.blocks = blk;
         a.gblock = gblock;
         a.nb = 1;

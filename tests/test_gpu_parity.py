@@ -476,3 +476,83 @@ def test_ingest_gives_identical_results():
         ctx.close()
     for k in res[0]:
         assert np.array_equal(res[0][k], res[1][k]), k
+
+
+def test_exit_locations_match_oracle_and_closed_form(abc_case):
+    import torch
+    fields, ref = abc_case                       # every particle leaves the 32^3 ABC block
+    ctx = bto.Context(N1, (0, 0, 0), H1, S1, L1)
+    for f in _dev(fields):
+        ctx.advect(f, DT1)
+    out = ctx.end_interval(exits=True)
+    ctx.check()
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    same = (g["exit_cycle"] == ref.exit_cycle) & (ref.min_margin >= 1e-4) & (ref.exit_cycle >= 0)
+    assert same.sum() > 3000
+    perr = np.max(np.abs(g["exit_pos"][same] - ref.exit_pos[same]) / np.asarray(H1))
+    terr = np.max(np.abs(g["exit_time"][same] - ref.exit_time[same]))
+    assert perr <= 1e-3 and terr <= 5e-3, (perr, terr)
+    # on a face: some coordinate at 0 or 1
+    on_face = np.min(np.minimum(np.abs(g["exit_pos"][same]), np.abs(g["exit_pos"][same] - 1.0)), axis=1)
+    assert np.max(on_face) < 1e-5
+    # straight flow: exact crossing x = 1 at time (1 - x0) / dt cycles
+    n, h, L, dt = (32, 32, 32), (1.0 / 32,) * 3, 50, 0.0099
+    ctx = bto.Context(n, (0, 0, 0), h, 2, L)
+    for f in _dev([inputs.uniform_field(n, (1.0, 0.0, 0.0))] * L):
+        ctx.advect(f, dt)
+    o = {k: v.cpu().numpy() for k, v in ctx.end_interval(exits=True).items()}
+    ctx.close()
+    t = o["valid"] == 0
+    assert t.sum() > 100 and np.all(np.isnan(o["exit_time"][~t]))
+    assert np.max(np.abs(o["exit_pos"][t, 0] - 1.0)) < 1e-6
+    assert np.max(np.abs(o["exit_time"][t] - (1.0 - o["seeds"][t, 0].astype(np.float64)) / dt)) < 1e-3
+
+
+def test_lattice_fill_matches_oracle():
+    import torch
+    rng = np.random.default_rng(21)
+    S = (37, 23, 19)
+    P = S[0] * S[1] * S[2]
+    ends = rng.standard_normal((P, 3)).astype(np.float32)
+    # missing entries in clusters, like terminations near block faces
+    valid = (rng.random(P) > 0.15).astype(np.uint8)
+    valid.reshape(S[2], S[1], S[0])[:, :, 10:14] = 0
+    valid.reshape(S[2], S[1], S[0])[5:8, :, :] = 0
+    out_o, st_o = oracle.fill_lattice(S, ends.astype(np.float64), valid)
+    d_out = torch.empty((P, 3), dtype=torch.float32, device="cuda")
+    d_st = torch.empty((P,), dtype=torch.uint8, device="cuda")
+    bto.bto_fill_lattice(S, torch.from_numpy(ends).cuda(), torch.from_numpy(valid).cuda(), d_out, d_st)
+    torch.cuda.synchronize()
+    st_g, out_g = d_st.cpu().numpy(), d_out.cpu().numpy()
+    assert np.array_equal(st_g, st_o)
+    ok = st_o > 0
+    assert np.max(np.abs(out_g[ok] - out_o[ok])) < 1e-5
+    assert np.all(np.isnan(out_g[~ok]))
+
+
+def test_stitching_matches_oracle():
+    import torch
+    rng = np.random.default_rng(22)
+    S, o, sp = (17, 13, 11), (0.2, -0.1, 0.3), (0.1, 0.12, 0.15)
+    P = S[0] * S[1] * S[2]
+    jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+    X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * np.asarray(sp) + np.asarray(o)
+    ends = []
+    for k in range(3):          # smooth random flow maps (+ a few missing entries)
+        E = X + 0.05 * np.sin(3 * X[:, [1, 2, 0]] + k) + 0.02 * k
+        E[rng.random(P) < 0.01] = np.nan
+        ends.append(E.astype(np.float32))
+    start = (np.asarray(o) + rng.random((500, 3)) * (np.asarray(S) - 1) * np.asarray(sp)).astype(np.float32)
+    ref = oracle.stitch(S, o, sp, [e.astype(np.float64) for e in ends], start.astype(np.float64))
+    dev_e = [torch.from_numpy(e).cuda() for e in ends]
+    table = torch.tensor([t.data_ptr() for t in dev_e], dtype=torch.int64, device="cuda")
+    path = torch.empty((4, 500, 3), dtype=torch.float32, device="cuda")
+    bto.bto_stitch_pathlines(S, o, sp, 3, table, 500, torch.from_numpy(start).cuda(), path)
+    torch.cuda.synchronize()
+    g = path.cpu().numpy()
+    assert np.array_equal(np.isnan(g), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.isnan(ref).any() and ok.any()
+    assert np.max(np.abs(g[ok] - ref[ok])) < 1e-5

@@ -310,3 +310,36 @@ def test_metrics_by_hand():
     assert oracle.max_l2(b, m) == 5.0
     assert oracle.accuracy_percent(0.25, 1.0) == pytest.approx(75.0)
     assert oracle.greatest_and_average_max_l2([1.0, 3.0, 2.0]) == (3.0, 2.0)
+
+
+# ----------------------------------------------------------------------------
+# Termination locations (the paper's future work, Sec. 6; chord clipping)
+# ----------------------------------------------------------------------------
+def test_exit_location_of_straight_flow_is_the_exact_crossing():
+    # Uniform u = (1, 0, 0): the chord is the path, so the clipped point is
+    # the exact face crossing and the exit time (in cycles) is (1 - x0)/dt.
+    n = (32, 32, 32)
+    h = (1.0 / 32,) * 3
+    g = oracle.Grid.make(n, (0.0, 0.0, 0.0), h)
+    field = inputs.uniform_field(n, (1.0, 0.0, 0.0))
+    L, dt = 50, 0.0099
+    st = oracle.run_interval(g, 2, L, dt, lambda c: field)
+    t = st.exit_cycle >= 0
+    assert t.sum() > 100
+    x0 = st.seeds[t]
+    assert np.max(np.abs(st.exit_pos[t, 0] - 1.0)) < 1e-12
+    assert np.array_equal(st.exit_pos[t, 1:], x0[:, 1:])
+    assert np.max(np.abs(st.exit_time[t] - (1.0 - x0[:, 0]) / dt)) < 1e-9
+    assert np.all(np.isnan(st.exit_time[~t]))
+
+
+def test_exit_location_for_each_stage_by_hand():
+    # The K dt = 3 linear-field cases of the stage-point pins above:
+    # p2 = -1 from x = 5 (t = 5/6, f = 1/2); p3 = 8.5 from x = 7 (t = 2/3,
+    # f = 1/2); p4 = -0.25 from x = 5 (t = 5/5.25, f = 1).
+    for x, xe, face, t, f in ((5.0, 1.0, 0.0, 5 / 6, 0.5), (7.0, 5.0, 8.0, 2 / 3, 0.5),
+                              (5.0, 4.0, 0.0, 5 / 5.25, 1.0)):
+        st = _one_cycle_1d(x, xe, 30.0, 0.1)
+        assert st.exit_pos[0, 0] == pytest.approx(face, abs=1e-12)
+        assert tuple(st.exit_pos[0, 1:]) == (4.0, 4.0)
+        assert st.exit_time[0] == pytest.approx(7 + t * f, abs=1e-12)

@@ -1,0 +1,83 @@
+"""Pins of the oracle's lattice reconstruction (Sec. 3.2, Eq. 1 and Eq. 2)."""
+import numpy as np
+
+import oracle
+
+
+def test_affine_flow_map_is_reconstructed_exactly():
+    # Linear interpolation reproduces an affine map, so every filled entry
+    # must equal the map itself.
+    rng = np.random.default_rng(3)
+    S = (9, 7, 6)
+    jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+    x0 = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3).astype(np.float64)
+    M = np.array([[1.1, 0.2, -0.3], [0.05, 0.9, 0.4], [-0.2, 0.1, 1.3]])
+    ends = x0 @ M.T + np.array([0.5, -1.0, 2.0])
+    valid = (rng.random(x0.shape[0]) > 0.3).astype(np.uint8)
+    out, status = oracle.fill_lattice(S, ends, valid)
+    filled = status == 2
+    assert filled.sum() > 50 and np.all(status[valid == 1] == 1)
+    assert np.max(np.abs(out[filled] - ends[filled])) < 1e-12
+
+
+def test_double_interpolation_identity():
+    # Eq. (2): interpolating inside [x0, x1] through the value filled at x1
+    # equals interpolating between x0 and x2 directly.
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((5, 3))
+    ends = f.copy()
+    valid = np.array([1, 0, 1, 1, 1], dtype=np.uint8)   # x0 = 0, x1 = 1 (missing), x2 = 2
+    out, status = oracle.fill_lattice((5, 1, 1), ends, valid)
+    assert status[1] == 2
+    for x in np.linspace(0.0, 1.0, 7):
+        through_fill = (x - 0) / (1 - 0) * out[1] + (1 - x) / (1 - 0) * out[0]
+        direct = (x - 0) / (2 - 0) * f[2] + (2 - x) / (2 - 0) * f[0]
+        assert np.allclose(through_fill, direct, atol=1e-14)
+
+
+def test_axis_with_the_closest_neighbours_is_used():
+    S = (7, 3, 1)
+    ends = np.arange(21 * 3, dtype=np.float64).reshape(21, 3)
+    valid = np.ones(21, dtype=np.uint8)
+    c = 3 + 7 * 1                      # centre (3, 1)
+    valid[[c, c - 1, c + 1, c - 2]] = 0  # x gap: a = 3, b = 2; y gap: a = b = 1
+    out, status = oracle.fill_lattice(S, ends, valid)
+    assert status[c] == 2
+    assert np.allclose(out[c], 0.5 * (ends[c - 7] + ends[c + 7]))
+    # an entry with no valid neighbour pair on any axis stays missing
+    out2, status2 = oracle.fill_lattice((3, 1, 1), ends[:3], np.array([0, 1, 1], dtype=np.uint8))
+    assert status2[0] == 0 and np.all(np.isnan(out2[0]))
+
+
+def _affine_lattice(S, o, sp, M, b):
+    jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+    X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * np.asarray(sp) + np.asarray(o)
+    return X @ M.T + b
+
+
+def test_stitching_composes_affine_flow_maps_exactly():
+    # Trilinear interpolation reproduces affine maps, so stitching through the
+    # basis flows of affine flow maps applies their composition exactly.
+    S, o, sp = (12, 10, 9), (0.0, 0.0, 0.0), (0.5, 0.5, 0.5)   # dyadic: exact lattice
+    M1 = np.array([[1.0, 0.05, 0.0], [-0.05, 1.0, 0.02], [0.0, 0.01, 0.98]])
+    M2 = np.array([[0.97, 0.0, 0.03], [0.02, 1.01, 0.0], [0.0, -0.02, 1.0]])
+    b1, b2 = np.array([0.1, -0.05, 0.2]), np.array([-0.1, 0.1, 0.05])
+    E1, E2 = _affine_lattice(S, o, sp, M1, b1), _affine_lattice(S, o, sp, M2, b2)
+    rng = np.random.default_rng(9)
+    start = rng.uniform(1.5, 3.5, size=(50, 3))
+    path = oracle.stitch(S, o, sp, [E1, E2], start)
+    want1 = start @ M1.T + b1
+    want2 = want1 @ M2.T + b2
+    assert np.max(np.abs(path[1] - want1)) < 1e-12
+    assert np.max(np.abs(path[2] - want2)) < 1e-12
+
+
+def test_stitching_at_lattice_points_and_outside():
+    S, o, sp = (4, 4, 4), (1.0, 1.0, 1.0), (0.25, 0.25, 0.25)
+    rng = np.random.default_rng(10)
+    E = rng.standard_normal((64, 3)) + 2.0
+    start = np.array([[1.25, 1.5, 1.0], [0.5, 1.5, 1.5], [1.75, 1.75, 1.75]])
+    path = oracle.stitch(S, o, sp, [E], start)
+    assert np.allclose(path[1, 0], E[1 + 4 * (2 + 4 * 0)])
+    assert np.all(np.isnan(path[1, 1]))                      # outside the lattice
+    assert np.allclose(path[1, 2], E[3 + 4 * (3 + 4 * 3)])   # upper corner
