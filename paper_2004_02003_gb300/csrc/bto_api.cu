@@ -43,7 +43,7 @@ struct bto_ctx {
     float4 *act[2] = {nullptr, nullptr};
     int32_t *gcnt[2] = {nullptr, nullptr};
     float4 *term = nullptr;
-    float4 *clip = nullptr;        // [P] clipped exit location (xi) and time per canonical id
+    float4 *clip = nullptr;        // [P] first outside point (xi) and stage per canonical id
     int64_t *diag_dst = nullptr;   // bto_copy_active scratch
     bto_status sticky = BTO_OK;
     // cached interval graph

@@ -138,19 +138,19 @@ __device__ __forceinline__ int rk4_step(float3 &x, const void *__restrict__ fiel
 // time is the cycle plus t times the fraction of the step at which q was
 // taken (1/2 for p2 and p3, 1 for p4 and the end point). A q with a NaN
 // component gives no direction: the location is x and t = 0.
-__device__ __forceinline__ float4 clip_exit(const Geo &g, float3 x, float3 q, int stage, int cycle) {
+__device__ __forceinline__ float4 clip_exit(float3 nf, float3 x, float3 q, int stage, int cycle) {
     if (!(q.x == q.x && q.y == q.y && q.z == q.z)) return make_float4(x.x, x.y, x.z, (float)cycle);
     float t = 1.f;
-    const float xs[3] = {x.x, x.y, x.z}, qs[3] = {q.x, q.y, q.z}, ns[3] = {g.fnx, g.fny, g.fnz};
+    const float xs[3] = {x.x, x.y, x.z}, qs[3] = {q.x, q.y, q.z}, ns[3] = {nf.x, nf.y, nf.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (qs[a] > ns[a]) t = fminf(t, (ns[a] - xs[a]) / (qs[a] - xs[a]));
         if (qs[a] < 0.f) t = fminf(t, (0.f - xs[a]) / (qs[a] - xs[a]));
     }
     t = fmaxf(t, 0.f);
-    const float cx = fminf(fmaxf(fmaf(t, q.x - x.x, x.x), 0.f), g.fnx);
-    const float cy = fminf(fmaxf(fmaf(t, q.y - x.y, x.y), 0.f), g.fny);
-    const float cz = fminf(fmaxf(fmaf(t, q.z - x.z, x.z), 0.f), g.fnz);
+    const float cx = fminf(fmaxf(fmaf(t, q.x - x.x, x.x), 0.f), nf.x);
+    const float cy = fminf(fmaxf(fmaf(t, q.y - x.y, x.y), 0.f), nf.y);
+    const float cz = fminf(fmaxf(fmaf(t, q.z - x.z, x.z), 0.f), nf.z);
     return make_float4(cx, cy, cz, (float)cycle + t * (stage <= 2 ? 0.5f : 1.f));
 }
 

@@ -46,7 +46,7 @@ struct AdvectArgs {
     int32_t *gcnt_out;           // [ngroups] survivors per group
     int64_t ngroups;
     float4 *term;                // [P] termination record per canonical id
-    float4 *clip;                // [P] clipped exit location (xi) and time, or NULL
+    float4 *clip;                // [P] first outside point (xi) and its RK4 stage, or NULL
     float dt;
 };
 

@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
                 } else {
                     const int64_t gid = idbase + __float_as_int(r[k].w);
                     __stcs(a.term + gid, make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
-                    if (a.clip) __stcs(a.clip + gid, clip_exit(g, x, q, failed, a.cycle));
+                    // first outside point and its stage; clipped at the interval end
+                    if (a.clip) __stcs(a.clip + gid, make_float4(q.x, q.y, q.z, __int_as_float(failed)));
                 }
             }
             const unsigned m = __ballot_sync(kFull, surv);
@@ -189,7 +190,10 @@ __global__ void write_term_kernel(const BlockDev *__restrict__ blocks, int32_t n
             if (valid) valid[gid] = 0;
             if (exit_cycle) exit_cycle[gid] = e;
             if (clip && (exit_pos || exit_time)) {
-                const float4 cl = clip[gid];
+                const float4 qs = clip[gid];
+                const float4 cl = clip_exit(make_float3((float)B.n[0], (float)B.n[1], (float)B.n[2]),
+                                            make_float3(r.x, r.y, r.z), make_float3(qs.x, qs.y, qs.z),
+                                            __float_as_int(qs.w), e);
                 if (exit_pos) {
                     exit_pos[3 * gid + 0] = fmaf(cl.x, B.h[0], B.origin[0]);
                     exit_pos[3 * gid + 1] = fmaf(cl.y, B.h[1], B.origin[1]);
