@@ -62,6 +62,7 @@ def parse():
                     help="field layout handed to the library (f4 pads each node to 16 bytes)")
     ap.add_argument("--ingest", action="store_true", help="repack F3 fields to 16-byte nodes per block (H1)")
     ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
+    ap.add_argument("--tile", default="", help="tx,ty,tz[,threads]: tiled advection kernel (default: off)")
     ap.add_argument("--fields", type=int, default=INTERVAL,
                     help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
                          "fewer fields make a small case for profiling")
@@ -337,6 +338,9 @@ def run_ours(args):
         # the library's autotuner picks the launch shape on this workload
         # (each of its 12 shapes runs one whole interval; then reseeded)
         tune = ctx.autotune(table, L, dt)
+    if args.tile:
+        tv = [int(v) for v in args.tile.split(",")]
+        ctx.set_tiling(tv[:3], tv[3] if len(tv) > 3 else 256)
     P = ctx.P
     out = ctx.alloc_outputs(dev)
 
@@ -431,6 +435,7 @@ def run_ours(args):
             "ingest": bool(args.ingest),
             "l2": f"inputs larger than L2: each cycle reads a 206 MB field; {nf} distinct fields resident",
             "launch": ctx.launch(),
+            "tiling": ctx.tiling(),
             "autotune_ms_per_cycle": tune["ms_per_cycle"] if tune else None,
             "parallelism": f"weak: {world} rank(s), each the full workload, no collective",
         },

@@ -214,21 +214,47 @@ BTO_API bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]);
 BTO_API bto_status bto_autotune(bto_ctx *ctx, const void *const *d_field_table, int32_t cycles,
                                 float dt, bto_stream stream, int32_t best[5], float ms[12]);
 
+/* Tiled advection (kernel K3t): the same cycle (Sec. 3.1, Eq. 1; results
+ * identical to the untiled kernel), organised around the field. Each
+ * block's cells are cut into tiles of tile_cells[0] x [1] x [2] cells
+ * (powers of two, 2..128 each; ragged at the upper faces). A persistent CTA
+ * stages, a few tiles ahead, each tile's nodes plus one cell of halo and the
+ * tile's particle records into shared memory with bulk asynchronous copies,
+ * advects the particles whose cell lies in the tile, and writes every
+ * survivor to the bucket of its new tile. Cells outside the staged box are
+ * gathered from global memory, so any speed is handled.
+ *   tile_cells       host int32[3]; NULL or {0,0,0} switches tiling off
+ *   threads_per_cta  128 or 256
+ * Allocates the buckets (about 2.3 x 16 bytes per particle, twice) on the
+ * first call; reseeds the interval (synchronously). Only at cycle 0, else
+ * BTO_ERR_STATE; BTO_ERR_STATE also with H1 ingest on; BTO_ERR_UNSUPPORTED
+ * when the staging buffers do not fit in shared memory or a tile has more
+ * than 4 * threads_per_cta - 2 staged node rows, (ty + 3) * (tz + 3). The
+ * autotuner times untiled shapes only (BTO_ERR_STATE while tiling is on). */
+BTO_API bto_status bto_set_tiling(bto_ctx *ctx, const int32_t tile_cells[3], int32_t threads_per_cta);
+
+/* Tiling in use (host ints: tile cells x, y, z, threads per CTA, grid,
+ * tiles, staging buffers per CTA, 1 if the particle records are staged with
+ * the nodes; all 0 when off). */
+BTO_API bto_status bto_get_tiling(const bto_ctx *ctx, int32_t out[8]);
+
 /* Diagnostics (not for the per-cycle path): copy the active particle list as
  * it stands before the next cycle.
  *   d_out  P*4 floats (device); for block b, rows offsets[b] ..
  *          offsets[b] + live[b] - 1 hold (xi_x, xi_y, xi_z, id bits) of its live
  *          particles, xi = (x - origin) / spacing in block-local cell units and
  *          id = canonical id within the block (int32 bits); other rows are
- *          unspecified
+ *          unspecified; with tiling on, the order inside a block is
+ *          unspecified too
  *   live   nb int32 (host): live particles per block
  * Waits for `stream`. */
 BTO_API bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live,
                                    bto_stream stream);
 
 /* Sticky error of earlier asynchronous work of this context (a launch
- * failure or a device-side error word); waits for the context's last stream
- * work; clears the sticky state. */
+ * failure, or BTO_ERR_TIMEOUT when a bounded device wait of the tiled
+ * kernel gave up); waits for the context's last stream work; clears the
+ * sticky state. */
 BTO_API bto_status bto_last_error(bto_ctx *ctx);
 
 /* ---- Post hoc reconstruction (Sec. 3.2, Sec. 3.3 Eq. 2) -----------------

@@ -59,6 +59,8 @@ def _declare(lib):
         "bto_launch_interval_graph": ([vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "bto_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
+        "bto_set_tiling": ([vp, c_i32p, ctypes.c_int32], ctypes.c_int),
+        "bto_get_tiling": ([vp, c_i32p], ctypes.c_int),
         "bto_autotune": ([vp, vp, ctypes.c_int32, ctypes.c_float, vp, c_i32p, c_fp], ctypes.c_int),
         "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
         "bto_last_error": ([vp], ctypes.c_int),
@@ -218,6 +220,19 @@ def bto_get_launch(ctx: int) -> dict:
             "reg_cap": buf[3], "grid": buf[4]}
 
 
+def bto_set_tiling(ctx: int, tile_cells, threads_per_cta: int = 256) -> None:
+    """tile_cells = None or (0, 0, 0) switches tiling off."""
+    arr = None if tile_cells is None else _arr(ctypes.c_int32, [int(v) for v in tile_cells])
+    _check(load().bto_set_tiling(ctx, arr, int(threads_per_cta)), "bto_set_tiling")
+
+
+def bto_get_tiling(ctx: int) -> dict:
+    buf = (ctypes.c_int32 * 8)()
+    _check(load().bto_get_tiling(ctx, buf), "bto_get_tiling")
+    return {"tile_cells": (buf[0], buf[1], buf[2]), "threads_per_cta": buf[3], "grid": buf[4], "tiles": buf[5],
+            "buffers": buf[6], "records_staged": buf[7]}
+
+
 AUTOTUNE_SHAPES = [(t, p, c) for t in (128, 256) for p in (1, 2, 4) for c in (0, 1)]
 
 
@@ -345,6 +360,12 @@ class Context:
 
     def launch(self):
         return bto_get_launch(self.handle)
+
+    def set_tiling(self, tile_cells, threads=256):
+        bto_set_tiling(self.handle, tile_cells, threads)
+
+    def tiling(self):
+        return bto_get_tiling(self.handle)
 
     def advect(self, field, dt, stream=None):
         bto_advect_cycle(self.handle, field, dt, stream)

@@ -51,12 +51,35 @@ struct bto_ctx {
     const void *const *gtable = nullptr;
     float gdt = 0.f;
     int gshape[5] = {0, 0, 0, 0, 0};
+    int gtiling = -1;
     cudaStream_t capture_stream = nullptr;
     // H1 ingest (F3 fields repacked to F4 per block, two buffers in flight)
     bool ingest = false;
     float4 *f4buf[2] = {nullptr, nullptr};
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ing_done[2] = {nullptr, nullptr}, adv_done[2] = {nullptr, nullptr};
+    // tiled advection (K3t): tile buckets, overflow region, rotating counts
+    bool tiled = false;
+    int32_t tdim[3] = {0, 0, 0};
+    int tnt = 128, tgrid = 0, tocc = 0;
+    size_t tsmem = 0;
+    int32_t tpitch = 0, tbox = 0, tbuf = 0, tnbuf = 2, tcap_max = 0, tstage_rec = 1;
+    int32_t ntiles = 0;
+    int64_t obase = 0, tslots = 0;
+    int tiling_gen = 0;
+    bto::TileDev *tiles = nullptr;
+    bto::BlockTiles *btiles = nullptr;
+    int32_t *unit_tile = nullptr;   // [obase/32] tile of each 32-slot unit of the buckets
+    int32_t *tseed = nullptr;       // [P] global id of the i-th seed
+    int64_t *tslot = nullptr;       // [P] its slot
+    int32_t *tcnt0 = nullptr;       // [ntiles] seeds per tile
+    int32_t *tcap = nullptr;        // [ntiles] bucket capacity (lim at seeding)
+    int32_t *tfront[2] = {nullptr, nullptr};
+    int32_t *tlim[2] = {nullptr, nullptr};
+    int32_t *tmv[3] = {nullptr, nullptr, nullptr};
+    int32_t *ocnt = nullptr;        // [3] overflow counts
+    float4 *tact[2] = {nullptr, nullptr};
+    int32_t *derr = nullptr;        // device error flag (bounded waits)
 };
 
 namespace {
@@ -108,8 +131,41 @@ void morton_order(const int32_t S[3], int32_t *out) {
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 
+void free_tiling(bto_ctx *c) {
+    cudaFree(c->tiles);
+    cudaFree(c->btiles);
+    cudaFree(c->unit_tile);
+    cudaFree(c->tseed);
+    cudaFree(c->tslot);
+    cudaFree(c->tcnt0);
+    cudaFree(c->tcap);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->tfront[k]);
+        cudaFree(c->tlim[k]);
+    }
+    for (int k = 0; k < 3; ++k) cudaFree(c->tmv[k]);
+    cudaFree(c->ocnt);
+    cudaFree(c->tact[0]);
+    cudaFree(c->tact[1]);
+    c->tiles = nullptr;
+    c->btiles = nullptr;
+    c->unit_tile = nullptr;
+    c->tseed = nullptr;
+    c->tslot = nullptr;
+    c->tcnt0 = nullptr;
+    c->tcap = nullptr;
+    for (int k = 0; k < 2; ++k) c->tfront[k] = c->tlim[k] = nullptr;
+    for (int k = 0; k < 3; ++k) c->tmv[k] = nullptr;
+    c->ocnt = nullptr;
+    c->tact[0] = c->tact[1] = nullptr;
+    c->tiled = false;
+    c->ntiles = 0;
+}
+
 void free_ctx(bto_ctx *c) {
     if (!c) return;
+    free_tiling(c);
+    cudaFree(c->derr);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     cudaFree(c->blocks);
@@ -161,10 +217,174 @@ int aux_grid(const bto_ctx *c) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((c->slots + 255) / 256, (int64_t)c->sm_count * 8));
 }
 
+// Counts of the tiled list at the start of cycle c.
+bto::TileCounts tile_counts(const bto_ctx *c, int cyc) {
+    return bto::TileCounts{c->tfront[cyc & 1], c->tmv[cyc % 3], c->tlim[cyc & 1]};
+}
+
+int tiled_aux_grid(const bto_ctx *c) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((c->tslots + 255) / 256, (int64_t)c->sm_count * 8));
+}
+
 bto_status seed(bto_ctx *c, cudaStream_t s) {
+    if (c->tiled) {
+        BTO_CUDA(bto::launch_seed_tiled(c->blocks, c->nb, c->tseed, c->tslot, c->P, c->tact[0], aux_grid(c), s));
+        const size_t tb = sizeof(int32_t) * (size_t)c->ntiles;
+        BTO_CUDA(cudaMemcpyAsync(c->tfront[0], c->tcnt0, tb, cudaMemcpyDeviceToDevice, s));
+        BTO_CUDA(cudaMemcpyAsync(c->tlim[0], c->tcap, tb, cudaMemcpyDeviceToDevice, s));
+        for (int k = 0; k < 3; ++k) BTO_CUDA(cudaMemsetAsync(c->tmv[k], 0, tb, s));
+        BTO_CUDA(cudaMemsetAsync(c->ocnt, 0, sizeof(int32_t) * 3, s));
+        c->cycle = 0;
+        return BTO_OK;
+    }
     BTO_CUDA(bto::launch_seed(c->blocks, c->gblock, c->perm, c->slots, group_size(c), c->act[0],
                               c->gcnt[0], aux_grid(c), s));
     c->cycle = 0;
+    return BTO_OK;
+}
+
+// Launch configuration of the tiled kernel for the current layout: as many
+// staging buffers (2..4) as fit beside the CTAs that should share an SM
+// (four CTAs of 128 threads, two of 256).
+bto_status configure_tiled(bto_ctx *c) {
+    const size_t box = bto::tiled_box_bytes(c->layout, c->tdim, &c->tpitch, &c->tbox);
+    int optin = 0, per_sm = 0;
+    BTO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    BTO_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+    const int want_ctas = c->tnt == 128 ? 4 : 2;
+    const size_t room = std::min<size_t>((size_t)optin, (size_t)per_sm / want_ctas - 1024);
+    // records ride with the box when two such buffers fit
+    size_t buf = box + 16 * (size_t)c->tcap_max;
+    c->tstage_rec = bto::tiled_smem_bytes(buf, 2) <= room ? 1 : 0;
+    if (!c->tstage_rec) buf = box;
+    c->tbuf = (int32_t)(buf / 4);
+    int nbuf = 4;
+    while (nbuf > 2 && bto::tiled_smem_bytes(buf, nbuf) > room) --nbuf;
+    const size_t smem = bto::tiled_smem_bytes(buf, nbuf);
+    if (smem > (size_t)optin) return BTO_ERR_UNSUPPORTED;
+    int occ = 0;
+    BTO_CUDA(bto::tiled_prepare(c->layout, c->tnt, smem, &occ));
+    if (occ < 1) return BTO_ERR_UNSUPPORTED;
+    c->tsmem = smem;
+    c->tnbuf = nbuf;
+    c->tocc = occ;
+    c->tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * occ, c->ntiles));
+    return BTO_OK;
+}
+
+// Tiles of every block, the seeds' buckets (seeds of a tile in Morton order
+// of the block's lattice) and the device arrays of the tiled path.
+bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
+    std::vector<bto::TileDev> tiles;
+    std::vector<bto::BlockTiles> bt((size_t)c->nb);
+    for (int32_t b = 0; b < c->nb; ++b) {
+        const BlockDev &B = c->blocks_h[(size_t)b];
+        int32_t ntl[3];
+        for (int a = 0; a < 3; ++a) ntl[a] = (B.n[a] + td[a] - 1) / td[a];
+        if ((int64_t)tiles.size() + (int64_t)ntl[0] * ntl[1] * ntl[2] > (1ll << 26)) return BTO_ERR_UNSUPPORTED;
+        bt[(size_t)b].first = (int32_t)tiles.size();
+        for (int a = 0; a < 3; ++a) bt[(size_t)b].nt[a] = ntl[a];
+        for (int32_t z = 0; z < ntl[2]; ++z)
+            for (int32_t y = 0; y < ntl[1]; ++y)
+                for (int32_t x = 0; x < ntl[0]; ++x) {
+                    bto::TileDev T{};
+                    T.b = b;
+                    const int32_t k[3] = {x, y, z};
+                    for (int a = 0; a < 3; ++a) {
+                        const int32_t c0 = k[a] * td[a], tn = std::min(td[a], B.n[a] - c0);
+                        T.lo[a] = std::max(c0 - 1, 0);
+                        T.hi[a] = std::min(c0 + tn + 1, B.n[a]);
+                    }
+                    T.n0 = (int64_t)T.lo[0] + (int64_t)B.nn[0] * ((int64_t)T.lo[1] + (int64_t)B.nn[1] * T.lo[2]);
+                    tiles.push_back(T);
+                }
+    }
+    const int64_t ntiles = (int64_t)tiles.size();
+    std::vector<int32_t> count((size_t)ntiles, 0);
+    std::vector<int32_t> tile_of((size_t)c->P);
+    std::vector<int32_t> order;
+    for (int32_t b = 0; b < c->nb; ++b) {
+        const BlockDev &B = c->blocks_h[(size_t)b];
+        order.resize((size_t)B.nseeds);
+        morton_order(B.S, order.data());
+        const bto::BlockTiles &T = bt[(size_t)b];
+        for (int64_t m = 0; m < B.nseeds; ++m) {
+            const int32_t p = order[(size_t)m];
+            const int32_t j[3] = {p % B.S[0], (p / B.S[0]) % B.S[1], p / (B.S[0] * B.S[1])};
+            int32_t k[3];
+            for (int a = 0; a < 3; ++a) k[a] = std::min(j[a] * B.stride, B.n[a] - 1) / td[a];
+            const int32_t t = T.first + k[0] + T.nt[0] * (k[1] + T.nt[1] * k[2]);
+            tile_of[(size_t)(B.base + m)] = t;
+            ++count[(size_t)t];
+        }
+    }
+    int64_t base = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int32_t n0 = count[(size_t)t];
+        const int64_t cap = ((int64_t)n0 + std::max<int64_t>(n0 / 4, 32) + 31) / 32 * 32;
+        tiles[(size_t)t].cap = (int32_t)cap;
+        tiles[(size_t)t].base = base;
+        base += cap;
+    }
+    const int64_t obase = base, tslots = obase + c->P;
+    int32_t cap_max = 0;
+    std::vector<int32_t> caps((size_t)ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) {
+        caps[(size_t)t] = tiles[(size_t)t].cap;
+        cap_max = std::max(cap_max, tiles[(size_t)t].cap);
+    }
+    std::vector<int32_t> unit_tile((size_t)(obase / bto::kUnit));
+    for (int64_t t = 0; t < ntiles; ++t)
+        for (int64_t u = tiles[(size_t)t].base / bto::kUnit; u < (tiles[(size_t)t].base + tiles[(size_t)t].cap) / bto::kUnit; ++u)
+            unit_tile[(size_t)u] = (int32_t)t;
+    std::vector<int32_t> fill((size_t)ntiles, 0);
+    std::vector<int32_t> tseed((size_t)c->P);
+    std::vector<int64_t> tslot((size_t)c->P);
+    for (int32_t b = 0; b < c->nb; ++b) {
+        const BlockDev &B = c->blocks_h[(size_t)b];
+        order.resize((size_t)B.nseeds);
+        morton_order(B.S, order.data());
+        for (int64_t m = 0; m < B.nseeds; ++m) {
+            const int64_t i = B.base + m;
+            const int32_t t = tile_of[(size_t)i];
+            tseed[(size_t)i] = (int32_t)(B.base + order[(size_t)m]);
+            tslot[(size_t)i] = tiles[(size_t)t].base + fill[(size_t)t]++;
+        }
+    }
+
+    free_tiling(c);
+    c->ntiles = (int32_t)ntiles;
+    c->obase = obase;
+    c->tslots = tslots;
+    cudaError_t e = cudaMalloc(&c->tiles, sizeof(bto::TileDev) * (size_t)ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->btiles, sizeof(bto::BlockTiles) * (size_t)c->nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->unit_tile, sizeof(int32_t) * std::max<size_t>(1, unit_tile.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&c->tseed, sizeof(int32_t) * (size_t)c->P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tslot, sizeof(int64_t) * (size_t)c->P);
+    const size_t tb = sizeof(int32_t) * (size_t)ntiles;
+    if (e == cudaSuccess) e = cudaMalloc(&c->tcnt0, tb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tcap, tb);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tfront[k], tb);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tlim[k], tb);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tmv[k], tb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ocnt, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tact[0], sizeof(float4) * (size_t)tslots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tact[1], sizeof(float4) * (size_t)tslots);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tiles, tiles.data(), sizeof(bto::TileDev) * (size_t)ntiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->btiles, bt.data(), sizeof(bto::BlockTiles) * (size_t)c->nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !unit_tile.empty())
+        e = cudaMemcpy(c->unit_tile, unit_tile.data(), sizeof(int32_t) * unit_tile.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tseed, tseed.data(), sizeof(int32_t) * (size_t)c->P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tslot, tslot.data(), sizeof(int64_t) * (size_t)c->P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tcnt0, count.data(), tb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tcap, caps.data(), tb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); free_tiling(c); return cuda_status(e); }
+    for (int a = 0; a < 3; ++a) c->tdim[a] = td[a];
+    c->tnt = nt;
+    c->tcap_max = cap_max;
+    c->tiled = true;
+    bto_status st = configure_tiled(c);
+    if (st != BTO_OK) { free_tiling(c); return st; }
     return BTO_OK;
 }
 
@@ -237,6 +457,8 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[1], sizeof(int32_t) * units);
     if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
     if (e == cudaSuccess) e = cudaMalloc(&c->clip, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->derr, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->derr, 0, sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(c->blocks, bl.data(), sizeof(BlockDev) * (size_t)nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -311,6 +533,51 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     if (c->cycle >= c->L) return BTO_ERR_STATE;
     if (c->ingest) return advect_ingest(c, field, fields, dt, s);
     const int cyc = c->cycle;
+    if (c->tiled) {
+        bto::TiledArgs a{};
+        a.blocks = c->blocks;
+        a.btiles = c->btiles;
+        a.tiles = c->tiles;
+        a.ntiles = c->ntiles;
+        a.nb = c->nb;
+        a.field = field;
+        a.fields = fields;
+        a.in = c->tact[cyc & 1];
+        a.out = c->tact[(cyc + 1) & 1];
+        a.cin = tile_counts(c, cyc);
+        a.front_out = c->tfront[(cyc + 1) & 1];
+        a.lim_out = c->tlim[(cyc + 1) & 1];
+        a.movein_out = c->tmv[(cyc + 1) % 3];
+        a.movein_zero = c->tmv[(cyc + 2) % 3];
+        a.ocnt_in = c->ocnt + cyc % 3;
+        a.ocnt_out = c->ocnt + (cyc + 1) % 3;
+        a.ocnt_zero = c->ocnt + (cyc + 2) % 3;
+        a.obase = c->obase;
+        a.ocap = c->P;
+        a.term = c->term;
+        a.clip = c->clip;
+        a.err = c->derr;
+        a.cycle = cyc;
+        a.dt = dt;
+        for (int k = 0; k < 3; ++k) {
+            int sh = 0;
+            while ((1 << sh) < c->tdim[k]) ++sh;
+            a.tsh[k] = sh;
+        }
+        a.pitch = c->tpitch;
+        a.box_floats = c->tbox;
+        a.buf_floats = c->tbuf;
+        a.stage_rec = c->tstage_rec;
+        a.nbuf = c->tnbuf;
+        cudaError_t e = bto::launch_advect_tiled(a, c->layout, c->tnt, c->tgrid, c->tsmem, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->sticky = cuda_status(e);
+            return c->sticky;
+        }
+        c->cycle = cyc + 1;
+        return BTO_OK;
+    }
     bto::AdvectArgs a{};
     a.blocks = c->blocks;
     a.gblock = c->gblock;
@@ -360,7 +627,13 @@ bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout) {
     const int old = ctx->layout;
     ctx->layout = layout == BTO_FIELD_F4_AOS ? bto::LAYOUT_F4 : bto::LAYOUT_F3;
     bto_status st = configure_launch(ctx);
-    if (st != BTO_OK) { ctx->layout = old; configure_launch(ctx); return st; }
+    if (st == BTO_OK && ctx->tiled) st = configure_tiled(ctx);
+    if (st != BTO_OK) {
+        ctx->layout = old;
+        configure_launch(ctx);
+        if (ctx->tiled) configure_tiled(ctx);
+        return st;
+    }
     drop_graph(ctx);
     return BTO_OK;
 }
@@ -368,7 +641,7 @@ bto_status bto_set_field_layout(bto_ctx *ctx, bto_field_layout layout) {
 bto_status bto_set_ingest(bto_ctx *ctx, int32_t enable) {
     if (!ctx || (enable != 0 && enable != 1)) return BTO_ERR_INVALID_ARG;
     if (ctx->cycle != 0) return BTO_ERR_STATE;
-    if (enable && ctx->layout != bto::LAYOUT_F3) return BTO_ERR_STATE;
+    if (enable && (ctx->layout != bto::LAYOUT_F3 || ctx->tiled)) return BTO_ERR_STATE;
     if (enable && !ctx->f4buf[0]) {
         int64_t maxn = 0;
         for (const BlockDev &B : ctx->blocks_h)
@@ -422,7 +695,7 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
     const bool same = ctx->gexec && ctx->gtable == d_field_table && ctx->gdt == dt &&
                       ctx->gshape[0] == ctx->layout && ctx->gshape[1] == ctx->nt &&
                       ctx->gshape[2] == ctx->ppt && ctx->gshape[3] == ctx->grid &&
-                      ctx->gshape[4] == (ctx->cap ? 1 : 0);
+                      ctx->gshape[4] == (ctx->cap ? 1 : 0) && ctx->gtiling == ctx->tiling_gen;
     if (!same) {
         drop_graph(ctx);
         if (!ctx->capture_stream)
@@ -454,6 +727,7 @@ bto_status bto_launch_interval_graph(bto_ctx *ctx, const void *const *d_field_ta
         ctx->gshape[2] = ctx->ppt;
         ctx->gshape[3] = ctx->grid;
         ctx->gshape[4] = ctx->cap ? 1 : 0;
+        ctx->gtiling = ctx->tiling_gen;
     }
     BTO_CUDA(cudaGraphLaunch(ctx->gexec, (cudaStream_t)stream));
     ctx->cycle = ctx->L;
@@ -472,9 +746,14 @@ bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends, uint
     cudaStream_t s = (cudaStream_t)stream;
     const int L = ctx->L;
     const int grid = aux_grid(ctx);
-    BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, ctx->act[L & 1], ctx->gcnt[L & 1],
-                                    ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
-                                    grid, s));
+    if (ctx->tiled)
+        BTO_CUDA(bto::launch_write_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[L & 1],
+                                              tile_counts(ctx, L), ctx->ocnt + L % 3, ctx->obase, ctx->P, d_ends,
+                                              d_valid, d_exit_cycle, tiled_aux_grid(ctx), s));
+    else
+        BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, ctx->act[L & 1], ctx->gcnt[L & 1],
+                                        ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
+                                        grid, s));
     BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
                                     d_valid, d_exit_cycle, grid, s, ctx->clip, d_exit_pos, d_exit_time));
     return seed(ctx, s);
@@ -515,6 +794,53 @@ bto_status bto_set_launch(bto_ctx *ctx, int32_t threads_per_cta, int32_t particl
     return BTO_OK;
 }
 
+bto_status bto_set_tiling(bto_ctx *ctx, const int32_t tile_cells[3], int32_t threads_per_cta) {
+    if (!ctx) return BTO_ERR_INVALID_ARG;
+    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    if (!tile_cells || (tile_cells[0] == 0 && tile_cells[1] == 0 && tile_cells[2] == 0)) {
+        if (ctx->tiled) {
+            BTO_CUDA(cudaDeviceSynchronize());
+            free_tiling(ctx);
+            ++ctx->tiling_gen;
+            drop_graph(ctx);
+            BTO_TRY(seed(ctx, 0));
+            BTO_CUDA(cudaDeviceSynchronize());
+        }
+        return BTO_OK;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (tile_cells[a] < 2 || tile_cells[a] > 128 || (tile_cells[a] & (tile_cells[a] - 1)))
+            return BTO_ERR_INVALID_ARG;
+    if (threads_per_cta != 128 && threads_per_cta != 256) return BTO_ERR_INVALID_ARG;
+    if (ctx->ingest) return BTO_ERR_STATE;
+    // every thread issues at most four copies per tile: staged rows + 2 record ranges
+    if ((int64_t)(tile_cells[1] + 3) * (tile_cells[2] + 3) + 2 > 4 * (int64_t)threads_per_cta)
+        return BTO_ERR_UNSUPPORTED;
+    int32_t pitch = 0, box = 0;
+    int optin = 0;
+    BTO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (bto::tiled_smem_bytes(bto::tiled_box_bytes(ctx->layout, tile_cells, &pitch, &box), 2) > (size_t)optin)
+        return BTO_ERR_UNSUPPORTED;
+    BTO_CUDA(cudaDeviceSynchronize());
+    BTO_TRY(build_tiling(ctx, tile_cells, threads_per_cta));
+    ++ctx->tiling_gen;
+    drop_graph(ctx);
+    BTO_TRY(seed(ctx, 0));
+    BTO_CUDA(cudaDeviceSynchronize());
+    return BTO_OK;
+}
+
+bto_status bto_get_tiling(const bto_ctx *ctx, int32_t out[8]) {
+    if (!ctx || !out) return BTO_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) out[a] = ctx->tiled ? ctx->tdim[a] : 0;
+    out[3] = ctx->tiled ? ctx->tnt : 0;
+    out[4] = ctx->tiled ? ctx->tgrid : 0;
+    out[5] = ctx->tiled ? ctx->ntiles : 0;
+    out[6] = ctx->tiled ? ctx->tnbuf : 0;
+    out[7] = ctx->tiled ? ctx->tstage_rec : 0;
+    return BTO_OK;
+}
+
 bto_status bto_get_launch(const bto_ctx *ctx, int32_t out[5]) {
     if (!ctx || !out) return BTO_ERR_INVALID_ARG;
     out[0] = ctx->nt;
@@ -530,7 +856,7 @@ bto_status bto_autotune(bto_ctx *ctx, const void *const *d_field_table, int32_t 
     if (!ctx || !d_field_table || !std::isfinite(dt)) return BTO_ERR_INVALID_ARG;
     if (cycles < 1 || cycles > ctx->L) return BTO_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(d_field_table) % alignof(void *)) return BTO_ERR_INVALID_ARG;
-    if (ctx->cycle != 0) return BTO_ERR_STATE;
+    if (ctx->cycle != 0 || ctx->tiled) return BTO_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int shapes[12][3] = {{128, 1, 0}, {128, 1, 1}, {128, 2, 0}, {128, 2, 1}, {128, 4, 0}, {128, 4, 1},
                                {256, 1, 0}, {256, 1, 1}, {256, 2, 0}, {256, 2, 1}, {256, 4, 0}, {256, 4, 1}};
@@ -588,6 +914,27 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
     if (reinterpret_cast<uintptr_t>(d_out) % 16) return BTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int cyc = ctx->cycle;
+    if (ctx->tiled) {
+        // per-block counts, then each block's particles from its offset on
+        if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)std::max<int64_t>(ctx->nb, ctx->slots / 32)));
+        BTO_CUDA(cudaMemsetAsync(ctx->diag_dst, 0, sizeof(int64_t) * (size_t)ctx->nb, s));
+        BTO_CUDA(bto::launch_count_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[cyc & 1],
+                                              tile_counts(ctx, cyc), ctx->ocnt + cyc % 3, ctx->obase, ctx->P,
+                                              ctx->diag_dst, tiled_aux_grid(ctx), s));
+        std::vector<int64_t> cnt((size_t)ctx->nb), start((size_t)ctx->nb);
+        BTO_CUDA(cudaMemcpyAsync(cnt.data(), ctx->diag_dst, sizeof(int64_t) * (size_t)ctx->nb, cudaMemcpyDeviceToHost, s));
+        BTO_CUDA(cudaStreamSynchronize(s));
+        for (int32_t b = 0; b < ctx->nb; ++b) {
+            start[(size_t)b] = ctx->blocks_h[(size_t)b].base;
+            live[b] = (int32_t)cnt[(size_t)b];
+        }
+        BTO_CUDA(cudaMemcpyAsync(ctx->diag_dst, start.data(), sizeof(int64_t) * (size_t)ctx->nb, cudaMemcpyHostToDevice, s));
+        BTO_CUDA(bto::launch_gather_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[cyc & 1],
+                                               tile_counts(ctx, cyc), ctx->ocnt + cyc % 3, ctx->obase, ctx->P,
+                                               ctx->diag_dst, reinterpret_cast<float4 *>(d_out), tiled_aux_grid(ctx), s));
+        BTO_CUDA(cudaStreamSynchronize(s));
+        return BTO_OK;
+    }
     const int G = group_size(ctx);
     const int64_t ng = ctx->slots / G;
     std::vector<int32_t> cnt((size_t)ng);
@@ -621,6 +968,13 @@ bto_status bto_last_error(bto_ctx *ctx) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaGetLastError();
     if (st == BTO_OK && e != cudaSuccess) st = cuda_status(e);
+    int32_t flag = 0;
+    if (e == cudaSuccess && ctx->derr) {
+        e = cudaMemcpy(&flag, ctx->derr, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && flag) e = cudaMemset(ctx->derr, 0, sizeof(int32_t));
+        if (st == BTO_OK && e != cudaSuccess) st = cuda_status(e);
+        if (st == BTO_OK && flag) st = BTO_ERR_TIMEOUT;
+    }
     ctx->sticky = BTO_OK;
     return st;
 }

@@ -88,15 +88,26 @@ __device__ __forceinline__ bool inside(const Geo &g, float x, float y, float z) 
     return x >= 0.f && x <= g.fnx && y >= 0.f && y <= g.fny && z >= 0.f && z <= g.fnz;
 }
 
+// Where a sampler takes a cell's corners from: GlobalSrc gathers them from
+// the block's node field in global memory; the tiled kernel's source reads a
+// shared-memory copy of the nodes around its tile and falls back to this one.
 template <int LAYOUT>
-__device__ __forceinline__ float3 sample(Cell &C, const void *__restrict__ field, const Geo &g,
-                                         float x, float y, float z) {
+struct GlobalSrc {
+    const void *field;
+    uint32_t nnx, nnxy;
+    __device__ __forceinline__ void load(int ix, int iy, int iz, float (&v)[8][3]) const {
+        load_cell<LAYOUT>(field, nnx, nnxy, ix, iy, iz, v);
+    }
+};
+
+template <class Src>
+__device__ __forceinline__ float3 sample(Cell &C, const Src &src, const Geo &g, float x, float y, float z) {
     // cell index clamp(floor(xi), 0, n-1): the upper face uses the last cell
     const int ix = min(max(__float2int_rd(x), 0), g.nx - 1);
     const int iy = min(max(__float2int_rd(y), 0), g.ny - 1);
     const int iz = min(max(__float2int_rd(z), 0), g.nz - 1);
     if (ix != C.ix || iy != C.iy || iz != C.iz) {
-        load_cell<LAYOUT>(field, g.nnx, g.nnxy, ix, iy, iz, C.v);
+        src.load(ix, iy, iz, C.v);
         C.ix = ix; C.iy = iy; C.iz = iz;
     }
     return trilerp(C.v, x - (float)ix, y - (float)iy, z - (float)iz);
@@ -106,30 +117,36 @@ __device__ __forceinline__ float3 sample(Cell &C, const void *__restrict__ field
 // when every tested point stays in the block; otherwise returns the stage
 // whose point left first (1 = p2, 2 = p3, 3 = p4, 4 = end point), leaves x
 // unchanged and stores that point in q.
-template <int LAYOUT>
-__device__ __forceinline__ int rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
-                                        const float3 s, float3 &q) {
+template <class Src>
+__device__ __forceinline__ int rk4_step_src(float3 &x, const Src &src, const Geo &g, const float3 s,
+                                            float3 &q) {
     const float3 hs = make_float3(0.5f * s.x, 0.5f * s.y, 0.5f * s.z);
     Cell C;
     C.ix = -1; C.iy = -1; C.iz = -1;
-    const float3 k1 = sample<LAYOUT>(C, field, g, x.x, x.y, x.z);
+    const float3 k1 = sample(C, src, g, x.x, x.y, x.z);
     float px = fmaf(hs.x, k1.x, x.x), py = fmaf(hs.y, k1.y, x.y), pz = fmaf(hs.z, k1.z, x.z);
     if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 1; }
-    const float3 k2 = sample<LAYOUT>(C, field, g, px, py, pz);
+    const float3 k2 = sample(C, src, g, px, py, pz);
     float3 acc = make_float3(k1.x + 2.f * k2.x, k1.y + 2.f * k2.y, k1.z + 2.f * k2.z);
     px = fmaf(hs.x, k2.x, x.x); py = fmaf(hs.y, k2.y, x.y); pz = fmaf(hs.z, k2.z, x.z);
     if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 2; }
-    const float3 k3 = sample<LAYOUT>(C, field, g, px, py, pz);
+    const float3 k3 = sample(C, src, g, px, py, pz);
     acc.x = fmaf(2.f, k3.x, acc.x); acc.y = fmaf(2.f, k3.y, acc.y); acc.z = fmaf(2.f, k3.z, acc.z);
     px = fmaf(s.x, k3.x, x.x); py = fmaf(s.y, k3.y, x.y); pz = fmaf(s.z, k3.z, x.z);
     if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 3; }
-    const float3 k4 = sample<LAYOUT>(C, field, g, px, py, pz);
+    const float3 k4 = sample(C, src, g, px, py, pz);
     acc.x += k4.x; acc.y += k4.y; acc.z += k4.z;
     const float sx6 = s.x * (1.f / 6.f), sy6 = s.y * (1.f / 6.f), sz6 = s.z * (1.f / 6.f);
     px = fmaf(sx6, acc.x, x.x); py = fmaf(sy6, acc.y, x.y); pz = fmaf(sz6, acc.z, x.z);
     if (!inside(g, px, py, pz)) { q = make_float3(px, py, pz); return 4; }
     x = make_float3(px, py, pz);
     return 0;
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ int rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
+                                        const float3 s, float3 &q) {
+    return rk4_step_src(x, GlobalSrc<LAYOUT>{field, g.nnx, g.nnxy}, g, s, q);
 }
 
 // Termination location (the paper's future work, Sec. 6): the chord from the

@@ -52,11 +52,103 @@ struct AdvectArgs {
 
 enum { LAYOUT_F3 = 0, LAYOUT_F4 = 1 };
 
+// Tiled advection (kernel K3t). Each block's cells are cut into tiles of
+// tx * ty * tz cells (ragged at the upper faces). A tile owns a bucket of
+// list slots [base, base + cap); the live particles whose cell lies in the
+// tile at the start of a cycle fill its first cnt slots. Particles whose
+// bucket is full go to an overflow region shared by all blocks.
+struct TileDev {
+    int32_t b;          // block
+    int32_t cap;        // bucket capacity (multiple of 32)
+    int64_t base;       // first slot of the bucket (multiple of 32)
+    int32_t lo[3];      // staged node box: first node per axis (first cell - 1, clamped)
+    int32_t hi[3];      // last node per axis (last cell + 2, clamped to n)
+    int64_t n0;         // node index of lo in the block's field
+};
+
+struct BlockTiles {
+    int32_t first;      // index of the block's first tile
+    int32_t nt[3];      // tiles per axis (x fastest)
+};
+
+// Per-tile counts of a tiled list. The home CTA of tile t writes its
+// surviving particles to the front of the bucket, [base, base + front[t]);
+// particles that move in from other tiles are appended from the back,
+// [base + cap - m, base + cap) with m = min(movein[t], lim[t]), where lim[t]
+// = cap - (particles of t when they moved), so the two ends never meet.
+struct TileCounts {
+    const int32_t *front;
+    const int32_t *movein;
+    const int32_t *lim;
+};
+
+// Arguments of one tiled cycle. front and lim are written (plain stores) for
+// every tile every cycle and ping-pong; movein counts are atomic and rotate
+// over three arrays (cycle c reads one, appends to the next and clears the
+// third). Overflow counts rotate likewise. List records are (xi, global id
+// bits). Tile extents are powers of two (tsh = log2).
+struct TiledArgs {
+    const BlockDev *blocks;
+    const BlockTiles *btiles;
+    const TileDev *tiles;
+    int32_t ntiles;
+    int32_t nb;
+    const void *field;           // single field pointer (nb == 1 calls), or NULL
+    const void *const *fields;   // device array [nb] used when field == NULL
+    const float4 *in;
+    float4 *out;
+    TileCounts cin;              // counts of the input list
+    int32_t *front_out;
+    int32_t *lim_out;
+    int32_t *movein_out;
+    int32_t *movein_zero;
+    const int32_t *ocnt_in;      // overflow counts (one int each)
+    int32_t *ocnt_out;
+    int32_t *ocnt_zero;
+    int64_t obase;               // first slot of the overflow region
+    int64_t ocap;                // its capacity (all particles)
+    float4 *term;
+    float4 *clip;
+    int32_t *err;                // set to 1 when a bounded wait gives up
+    int32_t cycle;
+    float dt;
+    int32_t tsh[3];              // log2 of the tile extent per axis
+    int32_t pitch;               // floats per staged node row
+    int32_t box_floats;          // floats of a staged box
+    int32_t buf_floats;          // floats per staging buffer (box, then up to cap_max records)
+    int32_t stage_rec;           // 1: particle records staged with the box; 0: read from the list
+    int32_t nbuf;                // staging buffers (2..4)
+};
+
 // Kernel launchers (bto_kernels.cu). Each returns cudaGetLastError().
 cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, bool cap, int grid,
                           size_t dyn_smem, cudaStream_t s);
 cudaError_t advect_occupancy(int layout, int nt, int ppt, bool cap, bool batched, size_t dyn_smem,
                              int *ctas_per_sm);
+// Tiled advection (bto_tiled.cu).
+// Staged box of one tile (bytes); pitch and box_floats as in TiledArgs.
+size_t tiled_box_bytes(int layout, const int32_t tdim[3], int32_t *pitch, int32_t *box_floats);
+// Dynamic shared memory of a CTA with nbuf staging buffers of buffer_bytes.
+size_t tiled_smem_bytes(size_t buffer_bytes, int nbuf);
+// nt = threads per CTA (128 or 256); ctas_per_sm = resident CTAs at smem.
+cudaError_t tiled_prepare(int layout, int nt, size_t smem, int *ctas_per_sm);
+cudaError_t launch_advect_tiled(const TiledArgs &a, int layout, int nt, int grid, size_t smem,
+                                cudaStream_t s);
+cudaError_t launch_seed_tiled(const BlockDev *blocks, int32_t nb, const int32_t *tseed,
+                              const int64_t *tslot, int64_t P, float4 *act, int grid, cudaStream_t s);
+cudaError_t launch_write_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
+                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt,
+                                    const int32_t *ocnt, int64_t obase, int64_t ocap, float *ends,
+                                    uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s);
+cudaError_t launch_gather_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
+                                     const int32_t *unit_tile, const float4 *act, TileCounts cnt,
+                                     const int32_t *ocnt, int64_t obase, int64_t ocap,
+                                     int64_t *cursor, float4 *out, int grid, cudaStream_t s);
+cudaError_t launch_count_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
+                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt,
+                                    const int32_t *ocnt, int64_t obase, int64_t ocap,
+                                    int64_t *per_block, int grid, cudaStream_t s);
+
 cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,
                         int64_t slots, int group, float4 *act, int32_t *gcnt, int grid,
                         cudaStream_t s);
