@@ -62,6 +62,7 @@ def parse():
                     help="field layout handed to the library (f4 pads each node to 16 bytes)")
     ap.add_argument("--ingest", action="store_true", help="repack F3 fields to 16-byte nodes per block (H1)")
     ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
+    ap.add_argument("--e2e-streams", type=int, default=4, help="copy streams of the end-to-end leg")
     ap.add_argument("--tile", default="", help="tx,ty,tz[,threads]: tiled advection kernel (default: off)")
     ap.add_argument("--fields", type=int, default=INTERVAL,
                     help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
@@ -290,14 +291,18 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
-def measured_traffic():
+def measured_traffic(launch):
     """DRAM bytes (read + write) of one advect launch from the committed ncu
-    capture, or None when the kernel source has changed since the capture."""
+    capture, or None when the kernel source has changed since the capture or
+    the capture was of another launch shape."""
     rec = os.path.join(ROOT, "profiles", "advect_turb256_traffic.json")
     if not os.path.exists(rec):
         return None
     d = json.load(open(rec))
-    return d["dram_bytes_per_launch"] if kernel_source_sha256().startswith(d["kernel_source_sha256_prefix"]) else None
+    if not kernel_source_sha256().startswith(d["kernel_source_sha256_prefix"]):
+        return None
+    shape = [launch["threads_per_cta"], launch["particles_per_thread"], launch["reg_cap"]]
+    return d["dram_bytes_per_launch"] if d.get("launch_shape") == shape else None
 
 
 def run_ours(args):
@@ -410,7 +415,7 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     algo = algorithmic_bytes(live, nodes_touched, L)
-    traffic = measured_traffic()
+    traffic = None if args.tile else measured_traffic(ctx.launch())
     achieved = float(algo.sum()) / advect_s / 1e9
     frac = achieved / peak
 
@@ -566,6 +571,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
 
     # (4) adjoint and batched workloads against the plain path (rank 0)
     if rank == 0:
+        res["tiled_ablation"] = tiled_leg(args, ext, org, spc, table, dt, out, dev, stream)
         res["adjoint"] = adjoint_leg(args, dev, stream)
         res["batched"] = batched_leg(args, dev, stream)
         if not args.no_large:
@@ -662,6 +668,39 @@ def batched_layout(seed=20040206, nb=512):
     return ext, org, spc, strides
 
 
+def tiled_leg(args, ext, org, spc, table, dt, ref_out, dev, stream,
+              shapes=((32, 8, 8, 256), (16, 16, 8, 256), (16, 8, 8, 128))):
+    """Ablation on the headline workload: the tiled advection kernel (field
+    tiles staged in shared memory by bulk copies, per-step rebinning) against
+    the untiled kernel, advect time only, and a bitwise comparison of every
+    output with the untiled interval."""
+    import torch
+    from paper_2004_02003_gb300 import bto
+    nb, L = len(ext), INTERVAL
+    rows = []
+    for sh in shapes:
+        ctx = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+        ctx.set_tiling(sh[:3], sh[3])
+        out = ctx.alloc_outputs(dev)
+        for rep in range(2):
+            ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(L)]
+            for c in range(L):
+                ev[c][0].record(stream)
+                ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+                ev[c][1].record(stream)
+            ctx.end_interval(out)
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+        same = all(torch.equal(out[k], ref_out[k]) for k in ("seeds", "ends", "valid", "exit_cycle"))
+        psteps = count_particle_steps(out["exit_cycle"].cpu().numpy(), L)
+        rows.append({"tile_cells": list(sh[:3]), "threads": sh[3], "tiling": ctx.tiling(),
+                     "advect_us_per_cycle": ms * 1e3 / L, "particle_steps_per_s": psteps / (ms / 1e3),
+                     "bitwise_equal_untiled": bool(same)})
+        ctx.close()
+    return rows
+
+
 def batched_leg(args, dev, stream):
     """Batched workload: 512 uneven blocks in one persistent launch per cycle
     (and as one CUDA graph per interval) against 512 single-block contexts,
@@ -734,17 +773,19 @@ def batched_leg(args, dev, stream):
             "terminated_frac": float((ex >= 0).mean())}
 
 
-def large_leg(args, dev, stream, nf=10):
+def large_leg(args, dev, stream):
     """Large in situ emulation: a 512^3-cell domain as 4 x 4 x 4 blocks of 128^3
     cells, one seed per cell (134,217,728 particles), 128 Fourier modes,
-    dt = 0.2 cell / max|u|, 3 intervals of 50 cycles; the batched form (one
-    launch per cycle) and the plain form (64 contexts, 64 launches per cycle)
-    side by side, and each interval against the global flow map (one block
-    over the whole domain: particles cross the block faces). The fields of
-    nf distinct cycles are resident (cycle c uses field c % nf), each 1.65 GB
-    for the blocks and 1.62 GB for the global grid."""
+    dt = 0.2 cell / max|u|, 3 intervals of 50 cycles. Every cycle the
+    stand-in simulation writes that cycle's field on the device (the global
+    513^3 node grid in single precision and its 64 block copies, timed
+    separately), then the batched form (one launch), the plain form (64
+    contexts, 64 launches) and the global flow map (one block over the whole
+    domain: particles cross the block faces) each take one cycle, and 1000
+    new pathlines take one RK4 step through the same field (ground truth for
+    the stitching of f3)."""
     import torch
-    from paper_2004_02003_gb300 import bto, inputs
+    from paper_2004_02003_gb300 import adjoint, bto, inputs
     G, n, S, L, NI = 512, 128, 1, 50, 3
     h = 1.0 / G
     dt = 0.2 * h
@@ -755,54 +796,76 @@ def large_leg(args, dev, stream, nf=10):
     org = [(b[0] * n * h, b[1] * n * h, b[2] * n * h) for b in blocks]
     spc = [(h, h, h)] * len(blocks)
     nb = len(blocks)
-    gfields, bfields = [], []
-    for c in range(nf):
-        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), c, dev)
-        gfields.append(gf)
-        bfields.append([gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous()
-                        for (bx, by, bz) in blocks])
-    torch.cuda.synchronize()
+
+    def simulate(cyc):
+        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), cyc, dev, dtype=torch.float32)
+        bf = [gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous()
+              for (bx, by, bz) in blocks]
+        return gf, bf
+
     bctx = bto.Context.batch(ext, org, spc, [S] * nb, L)
     gctx = bto.Context((G, G, G), (0, 0, 0), (h, h, h), S, L)
     plain = [bto.Context(ext[b], org[b], spc[b], S, L) for b in range(nb)]
     bout, gout = bctx.alloc_outputs(dev), gctx.alloc_outputs(dev)
     pouts = [p.alloc_outputs(dev) for p in plain]
-    def fidx(k, c):             # resident field of interval k, cycle c
-        return (k + c) % nf
-
-    tables = [torch.tensor([bfields[fidx(k, c)][b].data_ptr() for c in range(L) for b in range(nb)],
-                           dtype=torch.int64, device=dev) for k in range(NI)]
     # global id of each block seed (stride 1: seeds are the block's nodes)
     j = torch.arange(n ** 3, device=dev)
     jx, jy, jz = j % n, (j // n) % n, j // (n * n)
     gid = torch.cat([(jx + b[0] * n) + G * ((jy + b[1] * n) + G * (jz + b[2] * n)) for b in blocks])
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    t_b = t_p = 0.0
+    # new pathlines: starts well inside the domain (150 steps of at most
+    # 0.2 cells cannot reach a face), one RK4 step per cycle (1-cycle tape)
+    nq = 1000
+    starts = torch.from_numpy(np.random.default_rng(SEED + 5).uniform(0.1, 0.9, size=(nq, 3)).astype(np.float32)).to(dev)
+    tape = adjoint.Tape((G, G, G), (0, 0, 0), (h, h, h), nq, 1, 1)
+    cur, truth = starts.clone(), [starts.clone()]
+    tval = torch.empty((nq,), dtype=torch.uint8, device=dev)
+    t_sim = t_b = t_p = t_g = t_wb = 0.0
     report = []
     filled_sets, global_sets = [], []
     psteps_total = 0
     for k in range(NI):
-        ev[0].record(stream)
+        evs = []
         for c in range(L):
-            bctx.advect_batch(tables[k][c * nb:(c + 1) * nb], dt)
-        bctx.end_interval(bout)
-        ev[1].record(stream)
-        for c in range(L):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+            e[0].record(stream)
+            gf, bf = simulate(k * L + c)
+            table = torch.tensor([t.data_ptr() for t in bf], dtype=torch.int64, device=dev)
+            e[1].record(stream)
+            e[2].record(stream)
+            bctx.advect_batch(table, dt)
+            e[3].record(stream)
+            e[4].record(stream)
             for b in range(nb):
-                plain[b].advect(bfields[fidx(k, c)][b], dt)
+                plain[b].advect(bf[b], dt)
+            e[5].record(stream)
+            e[6].record(stream)
+            gctx.advect(gf, dt)
+            e[7].record(stream)
+            ftab = torch.tensor([gf.data_ptr()], dtype=torch.int64, device=dev)
+            nxt = torch.empty_like(cur)
+            bto.bto_tape_forward(tape.handle, cur, ftab, dt, nxt, tval, None)
+            cur = nxt
+            evs.append(e)
+            del gf, bf
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        bctx.end_interval(bout)
+        w1.record(stream)
         for b in range(nb):
             plain[b].end_interval(pouts[b])
-        ev[2].record(stream)
-        for c in range(L):
-            gctx.advect(gfields[fidx(k, c)], dt)
         gctx.end_interval(gout)
-        ev[3].record(stream)
         torch.cuda.synchronize()
-        t_b += ev[0].elapsed_time(ev[1])
-        t_p += ev[1].elapsed_time(ev[2])
+        truth.append(cur.clone())
+        for e in evs:
+            t_sim += e[0].elapsed_time(e[1])
+            t_b += e[2].elapsed_time(e[3])
+            t_p += e[4].elapsed_time(e[5])
+            t_g += e[6].elapsed_time(e[7])
+        t_wb += w0.elapsed_time(w1)
         bv = bout["valid"] == 1
         gv = gout["valid"][gid] == 1
-        d = ((bout["ends"][bv] - gout["ends"][gid][bv]).abs().amax(dim=1) / h).double()
+        both = bv & gv          # a BTO-valid particle can leave the domain in the global map only by rounding
+        d = ((bout["ends"][both] - gout["ends"][gid][both]).abs().amax(dim=1) / h).double()
         q = torch.quantile(d[torch.randperm(d.numel(), device=dev)[:1 << 24]],
                            torch.tensor([0.5, 0.99, 0.9999], dtype=torch.float64, device=dev)).tolist()
         dev_max = d.max().item()
@@ -831,8 +894,8 @@ def large_leg(args, dev, stream, nf=10):
                        "valid_end_deviation_cells_p50_p99_p9999": q,
                        "still_missing_after_fill": int((status == 0).sum().item()),
                        "total_average_l2": l2, "max_l2": mx,
-                       "accuracy_percent": (h - l2) / h * 100.0,
-                       "global_ms": ev[2].elapsed_time(ev[3])})
+                       "accuracy_percent": (h - l2) / h * 100.0})
+    tape.close()
     for p in plain:
         p.check()
     bctx.check(); gctx.check()
@@ -842,27 +905,14 @@ def large_leg(args, dev, stream, nf=10):
     bctx.close(); gctx.close()
     # new pathlines (Sec. 3.2 / 4.3 second context): stitched through the 3
     # intervals' basis flows of BTO (reconstructed) and of the global map,
-    # against an RK4 ground truth advected without interval resets (tape)
-    from paper_2004_02003_gb300 import adjoint
-    nq = 1000
-    starts = torch.from_numpy(np.random.default_rng(SEED + 5).uniform(0.1, 0.9, size=(nq, 3)).astype(np.float32)).to(dev)
+    # against the RK4 ground truth advected without interval resets
     paths = {}
     for name, sets in (("bto", filled_sets), ("global", global_sets)):
         table = torch.tensor([t.data_ptr() for t in sets], dtype=torch.int64, device=dev)
         path = torch.empty((NI + 1, nq, 3), dtype=torch.float32, device=dev)
         bto.bto_stitch_pathlines((G, G, G), (0, 0, 0), (h, h, h), NI, table, nq, starts, path)
         paths[name] = path
-    tape = adjoint.Tape((G, G, G), (0, 0, 0), (h, h, h), nq, L, 16)
-    cur, truth = starts.clone(), [starts.clone()]
-    for k in range(NI):
-        ftab = torch.tensor([gfields[fidx(k, c)].data_ptr() for c in range(L)], dtype=torch.int64, device=dev)
-        ends = torch.empty_like(cur)
-        val = torch.empty((nq,), dtype=torch.uint8, device=dev)
-        bto.bto_tape_forward(tape.handle, cur, ftab, dt, ends, val, None)
-        torch.cuda.synchronize()
-        cur = ends
-        truth.append(ends.clone())
-    tape.close()
+    torch.cuda.synchronize()
     path_err = []
     for k in range(1, NI + 1):
         row = {"after_interval": k}
@@ -874,11 +924,15 @@ def large_leg(args, dev, stream, nf=10):
             row[name + "_pathlines"] = int(fin.sum().item())
         path_err.append(row)
     maxes = [r["max_l2"] for r in report]
+    cyc = NI * L
     return {"workload": "512^3 cells as 4x4x4 blocks of 128^3, 1 seed per cell, 128 Fourier modes, "
-                        "3 intervals of 50 cycles, dt = 0.2 cell/max|u|",
-            "particles": P, "resident_fields": nf,
+                        "3 intervals of 50 cycles, dt = 0.2 cell/max|u|; each cycle's field generated on the "
+                        "device before the cycle (single-precision Fourier sum, timed separately)",
+            "particles": P,
             "batched_value": psteps_total / (t_b / 1e3), "plain_value": psteps_total / (t_p / 1e3),
-            "batched_ms_per_interval": t_b / NI, "plain_ms_per_interval": t_p / NI, "intervals": report,
+            "batched_advect_ms_per_cycle": t_b / cyc, "plain_advect_ms_per_cycle": t_p / cyc,
+            "global_advect_ms_per_cycle": t_g / cyc, "simulation_ms_per_cycle": t_sim / cyc,
+            "batched_writer_ms_per_interval": t_wb / NI, "intervals": report,
             "greatest_max_l2": max(maxes), "average_max_l2": float(np.mean(maxes)),
             "pathlines_vs_rk4_ground_truth": path_err}
 
@@ -897,9 +951,12 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
                 "ends": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
                 "valid": torch.empty((ctx.P,), dtype=torch.uint8, pin_memory=True),
                 "exit_cycle": torch.empty((ctx.P,), dtype=torch.int32, pin_memory=True)}
-    copy_stream = torch.cuda.Stream(device=dev)
+    # each cycle's block fields are split over K copy streams (each stream's
+    # copies run on a copy engine of its own when one is free)
+    K = max(1, min(args.e2e_streams, nb))
+    copy_streams = [torch.cuda.Stream(device=dev) for _ in range(K)]
     out_dev = ctx.alloc_outputs(dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
+    copied = [[torch.cuda.Event() for _ in range(K)] for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
     h2d_bytes = sum(t.numel() * 4 for t in host[0])
     d2h_bytes = sum(t.numel() * t.element_size() for t in out_host.values())
@@ -907,13 +964,15 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
     def step():
         for c in range(L):
             s = c & 1
-            with torch.cuda.stream(copy_stream):
-                if c >= 2:
-                    copy_stream.wait_event(consumed[s])
-                for b in range(nb):
-                    slots[s][b].copy_(host[c % R][b], non_blocking=True)
-                copied[s].record(copy_stream)
-            stream.wait_event(copied[s])
+            for k, cs in enumerate(copy_streams):
+                with torch.cuda.stream(cs):
+                    if c >= 2:
+                        cs.wait_event(consumed[s])
+                    for b in range(k, nb, K):
+                        slots[s][b].copy_(host[c % R][b], non_blocking=True)
+                    copied[s][k].record(cs)
+            for k in range(K):
+                stream.wait_event(copied[s][k])
             ctx.advect_batch(slot_ptrs[s], dt)
             consumed[s].record(stream)
         ctx.end_interval(out_dev)
@@ -930,7 +989,7 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
         units += step()
     el = time.perf_counter() - t
     return {"value": units / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
-            "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R}
+            "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R, "copy_streams": K}
 
 
 # ---------------------------------------------------------------------------

@@ -181,27 +181,32 @@ def fourier_field(modes: FourierModes, n, origin, h, cycle: int) -> np.ndarray:
     return np.ascontiguousarray(_fourier_eval(modes, x, y, z, cycle), dtype=np.float32)
 
 
-def fourier_field_torch(modes: FourierModes, n, origin, h, cycle: int, device):
+def fourier_field_torch(modes: FourierModes, n, origin, h, cycle: int, device, dtype=None):
     """Same field as :func:`fourier_field`, evaluated with torch on ``device``
     in float64 and rounded to float32. Used to synthesise large inputs
-    directly in device memory (the stand-in for the simulation)."""
+    directly in device memory (the stand-in for the simulation).
+
+    ``dtype=torch.float32`` evaluates the sum in single precision instead (a
+    field within ~1e-5 relative of the float64 one, about 30x faster on the
+    GPU): the per-cycle generator of the large in situ emulation."""
     import torch
-    x, y, z = (torch.as_tensor(v, dtype=torch.float64, device=device)
+    ft = torch.float64 if dtype is None else dtype
+    x, y, z = (torch.as_tensor(v, dtype=torch.float64, device=device).to(ft)
                for v in node_coords(n, origin, h))
-    k = torch.as_tensor(modes.k, dtype=torch.float64, device=device)
+    k = torch.as_tensor(modes.k, dtype=torch.float64, device=device).to(ft)
     tw = 2.0 * np.pi
-    X = torch.polar(torch.ones(len(x), modes.m, dtype=torch.float64, device=device),
+    X = torch.polar(torch.ones(len(x), modes.m, dtype=ft, device=device),
                     tw * torch.outer(x, k[:, 0]))
-    Y = torch.polar(torch.ones(len(y), modes.m, dtype=torch.float64, device=device),
+    Y = torch.polar(torch.ones(len(y), modes.m, dtype=ft, device=device),
                     tw * torch.outer(y, k[:, 1]))
-    Zs = torch.polar(torch.ones(len(z), modes.m, dtype=torch.float64, device=device),
+    Zs = torch.polar(torch.ones(len(z), modes.m, dtype=ft, device=device),
                      tw * torch.outer(z, k[:, 2]))
-    ph = torch.as_tensor(modes.phase + cycle * modes.drift, dtype=torch.float64, device=device)
-    amp = torch.as_tensor(modes.scale * modes.amp, dtype=torch.float64, device=device)
+    ph = torch.as_tensor(modes.phase + cycle * modes.drift, dtype=torch.float64, device=device).to(ft)
+    amp = torch.as_tensor(modes.scale * modes.amp, dtype=torch.float64, device=device).to(ft)
     W = torch.polar(amp, ph)
     T = (Zs[:, None, :] * Y[None, :, :]).reshape(-1, modes.m)
     Tr, Ti = T.real.contiguous(), T.imag.contiguous()
-    e = torch.as_tensor(modes.e, dtype=torch.float64, device=device)
+    e = torch.as_tensor(modes.e, dtype=torch.float64, device=device).to(ft)
     out = torch.empty((len(z), len(y), len(x), 3), dtype=torch.float32, device=device)
     for comp in range(3):
         G = (W * e[:, comp])[:, None] * X.T
