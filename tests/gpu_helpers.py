@@ -4,7 +4,8 @@ compare it with the FP64 oracle under the parity rule.
 Parity rule: for particles valid on both sides, every end-position component
 agrees within 1e-3 cell widths; valid flags agree except for particles whose
 oracle path (every tested stage point and end point) came within 1e-4 cell
-widths of a block face; those are counted.
+widths of a block face; those are counted. Seeds agree to the FP32 rounding
+of their physical coordinates (2^-23 |x|, plus 1e-6 cells).
 """
 from __future__ import annotations
 
@@ -38,8 +39,11 @@ def compare(gpu, ref, h, tol=END_TOL_CELLS, face_eps=FACE_EPS_CELLS, ids=None):
     flag_diff = g_valid != ref.valid
     bad = flag_diff & ~near
     assert not bad.any(), f"{int(bad.sum())} valid flags differ away from faces"
-    seed_err = np.max(np.abs(g_seeds - ref.seeds) / h) if len(h) else 0.0
-    assert seed_err <= 1e-5, f"seed positions differ by {seed_err} cells"
+    # seeds: the GPU writes origin + xi h in FP32 (one rounding, at most half
+    # an ulp of |x|), the oracle the same sum in FP64 from the same inputs
+    seed_excess = np.abs(g_seeds - ref.seeds) - (2.0 ** -23 * np.abs(ref.seeds) + 1e-6 * h)
+    seed_err = float(np.max(seed_excess / h)) if seed_excess.size else 0.0
+    assert seed_err <= 0.0, f"seed positions differ by {seed_err} cells beyond FP32 rounding"
     both = (g_valid == 1) & (ref.valid == 1)
     err = float(np.max(np.abs(g_ends[both] - ref.x[both]) / h)) if both.any() else 0.0
     assert err <= tol, f"end positions differ by {err} cells (tol {tol})"

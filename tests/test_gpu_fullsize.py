@@ -1,11 +1,17 @@
-"""Full-size parity: the benchmark's workload (256^3 cells as 2x2x2 blocks of
-128^3, stride 2, 2,097,152 particles, 100 cycles) in the benchmark's launch
-configuration, against the FP64 oracle on sampled particles, plus the Eq. (hx)
-invariant on every particle.
+"""Full-size parity at the workloads' own sizes, each in the launch
+configuration the benchmark times, against the FP64 oracle on sampled
+particles (the oracle advances particles independently, so a sample is exact
+for its particles), plus the Eq. (hx) invariant on every particle:
 
-The fields are synthesised on the host (the seeded generator module, in
-float64, rounded to float32) and copied to the device, so both sides read
-identical inputs.
+* the headline workload: 256^3 cells as 2x2x2 blocks of 128^3, stride 2,
+  2,097,152 particles, 100 cycles (fields synthesised on the host in float64,
+  rounded to float32, and copied to the device);
+* the batched workload: 512 uneven blocks, about 44M particles, 64 cycles
+  (fields generated on the device; the sampled blocks' fields are copied
+  back for the oracle);
+* the large in situ workload: 64 blocks of 128^3, 134M particles, first
+  interval of 50 cycles (every cycle's field generated on the device; the
+  probed block's field is copied back each cycle).
 """
 import numpy as np
 import pytest
@@ -80,3 +86,109 @@ def test_turb256_full_size_sampled_parity(cuda_device):
         assert far.sum() > 0
         assert np.all(gpu["valid"][off[b]:off[b + 1]][far] == 1)
     assert 0.01 < 1.0 - gpu["valid"].mean() < 0.5
+
+
+def test_batched512_full_size_sampled_parity(cuda_device):
+    """The batched workload (512 uneven blocks, strides 1/2/4, double gyre +
+    32 Fourier modes, 64 cycles, about 44M particles) in the benchmark's
+    launch configuration (the autotuner's pick), against the FP64 oracle on
+    2048 sampled particles of 8 sampled blocks, plus the Eq. (hx) invariant
+    on every particle of every block."""
+    import torch
+    from paper_2004_02003_gb300 import build
+    build.build()
+    ext, org, spc, strides = bench.batched_layout()
+    nb, L, NF = len(ext), 64, 4
+    modes = inputs.fourier_modes(bench.SEED + 2, m=32, kmin=1.0, kmax=16.0, drift_max=0.05)
+    vmax = np.pi * inputs.DG_A * 1.5 + 0.1
+    dt = 0.25 * min(min(h) for h in spc) / vmax
+    fields = [[inputs.double_gyre_fourier_torch(modes, ext[b], org[b], spc[b], c * dt, c, cuda_device)
+               for b in range(nb)] for c in range(NF)]
+    table = torch.tensor([fields[c % NF][b].data_ptr() for c in range(L) for b in range(nb)],
+                         dtype=torch.int64, device=cuda_device)
+    ctx = bto.Context.batch(ext, org, spc, strides, L)
+    ctx.autotune(table, 16, dt)
+    for c in range(L):
+        ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    out = ctx.end_interval()
+    ctx.check()
+    torch.cuda.synchronize()
+    off = ctx.offsets()
+    ctx.close()
+    rng = np.random.default_rng(bench.SEED + 7)
+    for b in sorted(rng.choice(nb, size=8, replace=False)):
+        g = oracle.Grid.make(ext[b], org[b], spc[b])
+        P_b = oracle.num_seeds(g, strides[b])
+        ids = np.sort(rng.choice(P_b, size=min(2048, P_b), replace=False))
+        host = [fields[c][b].cpu().numpy() for c in range(NF)]
+        ref = oracle.run_interval(g, strides[b], L, dt, lambda c: host[c % NF], ids=ids)
+        sub = {k: v[off[b]:off[b + 1]].cpu().numpy() for k, v in out.items()}
+        compare(sub, ref, spc[b], ids=ids)
+    # Eq. (hx) on every particle: |u| <= vmax everywhere, so a seed farther
+    # than L dt vmax from every face of its block stays valid
+    reach = L * dt * vmax
+    seeds = out["seeds"].double()
+    valid = out["valid"]
+    nfar = 0
+    for b in range(nb):
+        lo = torch.tensor(org[b], dtype=torch.float64, device=cuda_device)
+        hi = lo + torch.tensor([ext[b][a] * spc[b][a] for a in range(3)], dtype=torch.float64, device=cuda_device)
+        s = seeds[off[b]:off[b + 1]]
+        d = torch.minimum(s - lo, hi - s).amin(dim=1)
+        far = d > reach + 1e-9
+        nfar += int(far.sum().item())
+        assert bool((valid[off[b]:off[b + 1]][far] == 1).all()), b
+    assert nfar > 1000000
+
+
+def test_large_full_size_sampled_parity(cuda_device):
+    """The large in situ workload (512^3 cells as 64 blocks of 128^3, one seed
+    per cell: 134,217,728 particles), its first interval of 50 cycles, with
+    every cycle's field generated on the device as the benchmark does, in
+    the benchmark's launch configuration: 4096 sampled particles of one
+    interior block against the FP64 oracle on that block's field copied back
+    each cycle, plus the Eq. (hx) invariant on every particle."""
+    import torch
+    from paper_2004_02003_gb300 import build
+    build.build()
+    G, n, S, L = 512, 128, 1, 50
+    h = 1.0 / G
+    dt = 0.2 * h
+    nbx = G // n
+    modes = inputs.fourier_modes(bench.SEED + 4, m=128, kmin=1.0, kmax=16.0, drift_max=0.05)
+    blocks = [(bx, by, bz) for bz in range(nbx) for by in range(nbx) for bx in range(nbx)]
+    ext = [(n, n, n)] * len(blocks)
+    org = [(b[0] * n * h, b[1] * n * h, b[2] * n * h) for b in blocks]
+    spc = [(h, h, h)] * len(blocks)
+    nb = len(blocks)
+    probe = blocks.index((1, 2, 1))
+    g = oracle.Grid.make(ext[probe], org[probe], spc[probe])
+    ids = np.sort(np.random.default_rng(bench.SEED + 8).choice(n ** 3, size=4096, replace=False))
+    st = oracle.State(oracle.seeds(g, S, ids))
+    ctx = bto.Context.batch(ext, org, spc, [S] * nb, L)
+    vmax = 0.0
+    for c in range(L):
+        gf = inputs.fourier_field_torch(modes, (G, G, G), (0, 0, 0), (h, h, h), c, cuda_device, dtype=torch.float32)
+        vmax = max(vmax, float(torch.linalg.vector_norm(gf, dim=-1).max().item()))
+        bf = [gf[bz * n: bz * n + n + 1, by * n: by * n + n + 1, bx * n: bx * n + n + 1].contiguous()
+              for (bx, by, bz) in blocks]
+        table = torch.tensor([t.data_ptr() for t in bf], dtype=torch.int64, device=cuda_device)
+        ctx.advect_batch(table, dt)
+        oracle.cycle(g, bf[probe].cpu().numpy(), dt, c, st)
+        torch.cuda.synchronize()
+        del gf, bf
+    out = ctx.end_interval()
+    ctx.check()
+    torch.cuda.synchronize()
+    off = ctx.offsets()
+    ctx.close()
+    sub = {k: v[off[probe]:off[probe + 1]].cpu().numpy() for k, v in out.items()}
+    rep = compare(sub, st, spc[probe], ids=ids)
+    assert rep["both_valid"] > 3000
+    reach = L * dt * vmax
+    seeds = out["seeds"].double()
+    blo = torch.tensor(org, dtype=torch.float64, device=cuda_device).repeat_interleave(n ** 3, dim=0)
+    d = torch.minimum(seeds - blo, blo + n * h - seeds).amin(dim=1)
+    far = d > reach + 1e-9
+    assert int(far.sum().item()) > 50000000
+    assert bool((out["valid"][far] == 1).all())
