@@ -947,10 +947,12 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
             host[r][b].copy_(fields[r][b])
     slots = [[torch.empty_like(f) for f in fields[0]] for _ in range(2)]
     slot_ptrs = [torch.tensor([t.data_ptr() for t in s], dtype=torch.int64, device=dev) for s in slots]
-    out_host = {"seeds": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
+    def host_out():
+        return {"seeds": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
                 "ends": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
                 "valid": torch.empty((ctx.P,), dtype=torch.uint8, pin_memory=True),
                 "exit_cycle": torch.empty((ctx.P,), dtype=torch.int32, pin_memory=True)}
+    out_host = [host_out(), host_out()]      # interval k's results land in out_host[k % 2]
     # each cycle's block fields are split over K copy streams (each stream's
     # copies run on a copy engine of its own when one is free)
     K = max(1, min(args.e2e_streams, nb))
@@ -958,35 +960,49 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
     out_dev = ctx.alloc_outputs(dev)
     copied = [[torch.cuda.Event() for _ in range(K)] for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
+    landed = [torch.cuda.Event() for _ in range(2)]
     h2d_bytes = sum(t.numel() * 4 for t in host[0])
-    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host.values())
+    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host[0].values())
+    gc = [0]                                   # cycles enqueued so far (slot parity)
 
-    def step():
+    def enqueue(k):
+        """Interval k: per cycle, the fields' host-to-device copies (two-slot
+        device ring, copies of the next cycle overlap the current advection),
+        the advection, then the writer and the results' copy back."""
         for c in range(L):
-            s = c & 1
-            for k, cs in enumerate(copy_streams):
+            s = gc[0] & 1
+            for j, cs in enumerate(copy_streams):
                 with torch.cuda.stream(cs):
-                    if c >= 2:
+                    if gc[0] >= 2:
                         cs.wait_event(consumed[s])
-                    for b in range(k, nb, K):
+                    for b in range(j, nb, K):
                         slots[s][b].copy_(host[c % R][b], non_blocking=True)
-                    copied[s][k].record(cs)
-            for k in range(K):
-                stream.wait_event(copied[s][k])
+                    copied[s][j].record(cs)
+            for j in range(K):
+                stream.wait_event(copied[s][j])
             ctx.advect_batch(slot_ptrs[s], dt)
             consumed[s].record(stream)
+            gc[0] += 1
         ctx.end_interval(out_dev)
-        for k in out_host:
-            out_host[k].copy_(out_dev[k], non_blocking=True)
-        stream.synchronize()
-        return count_particle_steps(out_host["exit_cycle"].numpy(), L)
+        for key in out_dev:
+            out_host[k % 2][key].copy_(out_dev[key], non_blocking=True)
+        landed[k % 2].record(stream)
 
-    for _ in range(max(1, args.warmup)):
-        step()
+    def run(n):
+        """n intervals, each enqueued before the previous one's results are
+        read on the host, so that the copy engines never wait for the host."""
+        units = 0
+        for k in range(n + 1):
+            if k < n:
+                enqueue(k)
+            if k >= 1:
+                landed[(k - 1) % 2].synchronize()
+                units += count_particle_steps(out_host[(k - 1) % 2]["exit_cycle"].numpy(), L)
+        return units
+
+    run(max(1, args.warmup))
     t = time.perf_counter()
-    units = 0
-    for _ in range(args.steps):
-        units += step()
+    units = run(args.steps)
     el = time.perf_counter() - t
     return {"value": units / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
             "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R, "copy_streams": K}
