@@ -1035,7 +1035,42 @@ def cpu_baseline(fields, dt, seconds, org):
         done.append(f"block {b}: cycles 0..{c - 1}")
     return {"value": steps / spent, "unit": "particle-steps/s", "cores": nthreads, "host_cpus": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"turb256 workload, {'; '.join(done)} ({steps} particle-steps, {spent:.1f} s of oracle time)"}
+            "sample": f"turb256 workload, {'; '.join(done)} ({steps} particle-steps, {spent:.1f} s of oracle time)",
+            "other_configs": oracle_other_configs()}
+
+
+def oracle_other_configs():
+    """The oracle's rate on the ABC block (all 4096 seeds, 50 cycles) and on
+    the adjoint workload (4096 of its 32,768 seeds, 200 cycles: forward, and
+    forward plus the discrete adjoint)."""
+    import oracle
+    from paper_2004_02003_gb300 import inputs
+    res = {}
+    n, h, L, dt = (32, 32, 32), (1.0 / 32,) * 3, 50, 0.01
+    fields = [inputs.abc_field(n, (0, 0, 0), h, c * dt) for c in range(L)]
+    g = oracle.Grid.make(n, (0, 0, 0), h)
+    t = time.perf_counter()
+    st = oracle.run_interval(g, 2, L, dt, lambda c: fields[c])
+    el = time.perf_counter() - t
+    res["abc_32"] = {"particle_steps": count_particle_steps(st.exit_cycle, L),
+                     "particle_steps_per_s": count_particle_steps(st.exit_cycle, L) / el}
+    n, L, dt = (64, 64, 64), 200, 0.01
+    h = (2 * np.pi / 64,) * 3
+    fields = [inputs.abc_field(n, (0, 0, 0), h, c * dt) for c in range(L)]
+    g = oracle.Grid.make(n, (0, 0, 0), h)
+    seeds = oracle.seeds(g, 2)
+    ids = np.sort(np.random.default_rng(SEED + 9).choice(seeds.shape[0], size=4096, replace=False))
+    t = time.perf_counter()
+    st, _ = oracle.forward_with_history(g, lambda c: fields[c], dt, seeds[ids], L)
+    t_f = time.perf_counter() - t
+    up = 2.0 * (st.x - seeds[ids]) * st.valid[:, None]
+    t = time.perf_counter()
+    oracle.vjp(g, lambda c: fields[c], dt, seeds[ids], L, up, want_field_grads=True)
+    t_fb = time.perf_counter() - t
+    ps = count_particle_steps(st.exit_cycle, L)
+    res["adjoint_64"] = {"sample_seeds": 4096, "particle_steps": ps, "forward_particle_steps_per_s": ps / t_f,
+                         "forward_backward_s": t_fb, "forward_backward_particle_steps_per_s": ps / t_fb}
+    return res
 
 
 def run_reference(args):
