@@ -274,11 +274,21 @@ def touched_nodes(ctx, act, n_cells, nb):
 
 
 def algorithmic_bytes(live, nodes_touched, L):
-    """SURVEY-defined algorithmic bytes of cycle c:
+    """Algorithmic bytes of cycle c (what the method must move):
     12 * nodes touched + 24 * live at start + 17 * terminated in the cycle."""
     term = np.zeros(L, dtype=np.int64)
     term[:-1] = live[:-1] - live[1:]
     return 12 * nodes_touched + 24 * live + 17 * term
+
+
+def hbm_peak():
+    """HBM bandwidth denominator (GB/s): the measured copy bandwidth of this
+    pool's GB300s when the measurement file is present, else 6800 GB/s."""
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(pk)) if os.path.exists(pk) else {}
+    if "hbm_gbs" in peaks:
+        return float(peaks["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
 
 
 def kernel_source_sha256():
@@ -408,12 +418,7 @@ def run_ours(args):
     # launch (12 B per touched node, 24 B per live particle, 17 B per
     # termination) over the measured launch durations
     import json as _json
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = _json.load(open(pk))
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak, peak_src = hbm_peak()
     algo = algorithmic_bytes(live, nodes_touched, L)
     traffic = None if args.tile else measured_traffic(ctx.launch())
     achieved = float(algo.sum()) / advect_s / 1e9
@@ -763,6 +768,28 @@ def batched_leg(args, dev, stream):
         p.check()
         p.close()
     P = ctx.P
+    # roofline of the batched launch: algorithmic bytes (12 per node of the
+    # cells holding a live particle, 24 per live particle, 17 per
+    # termination) over the advect-only time of one interval; the touched
+    # nodes are counted at every 8th cycle and held in between
+    act = torch.empty((P, 4), dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(L)]
+    touched = np.zeros(L, dtype=np.int64)
+    for c in range(L):
+        if c % 8 == 0:
+            touched[c] = touched_nodes_multi(ctx, act, ext)
+        else:
+            touched[c] = touched[c - 1]
+        ev[c][0].record(stream)
+        ctx.advect_batch(table[c * nb:(c + 1) * nb], dt)
+        ev[c][1].record(stream)
+    ctx.end_interval(out)
+    torch.cuda.synchronize()
+    ctx.check()
+    advect_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    algo = algorithmic_bytes(live_per_cycle(out["exit_cycle"].cpu().numpy(), L), touched, L)
+    peak, peak_src = hbm_peak()
+    achieved = float(algo.sum()) / (advect_ms / 1e3) / 1e9
     ctx.close()
     return {"workload": "512 uneven blocks (16..96 cells per axis, aspect <= 3), strides {1,2,4}, "
                         "double gyre + 32 Fourier modes, interval 64",
@@ -770,7 +797,36 @@ def batched_leg(args, dev, stream):
             "batched_value": psteps / (t_b / 1e3), "graph_value": psteps / (t_g / 1e3),
             "plain_value": psteps / (t_p / 1e3), "batched_vs_plain": t_p / t_b,
             "ms_per_interval": {"batched": t_b, "graph": t_g, "plain": t_p},
-            "terminated_frac": float((ex >= 0).mean())}
+            "terminated_frac": float((ex >= 0).mean()),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src, "advect_ms_per_interval": advect_ms,
+                         "nodes_touched_frac": float(touched.mean() / nodes)}}
+
+
+def touched_nodes_multi(ctx, act, ext):
+    """touched_nodes for blocks of any extents: the nodes of the cells that
+    hold a live particle at the start of the current cycle, all blocks."""
+    import torch
+    live = ctx.copy_active(act)
+    off = ctx.offsets()
+    dev = act.device
+    nb = len(ext)
+    n = torch.tensor(ext, dtype=torch.int64, device=dev)                   # (nb, 3) cells
+    nn = n + 1
+    nodes = nn.prod(dim=1)
+    base = torch.cumsum(nodes, 0) - nodes
+    idx = torch.cat([torch.arange(off[b], off[b] + live[b], device=dev) for b in range(nb) if live[b] > 0])
+    bid = torch.repeat_interleave(torch.arange(nb, device=dev),
+                                  torch.tensor(live, dtype=torch.int64, device=dev))
+    x = act[idx, :3]
+    cell = torch.minimum(torch.clamp(torch.floor(x).to(torch.int64), min=0), n[bid] - 1)
+    mark = torch.zeros(int(nodes.sum().item()), dtype=torch.bool, device=dev)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                k = (cell[:, 0] + dx) + nn[bid, 0] * ((cell[:, 1] + dy) + nn[bid, 1] * (cell[:, 2] + dz))
+                mark[base[bid] + k] = True
+    return int(mark.sum().item())
 
 
 def large_leg(args, dev, stream):
