@@ -417,7 +417,6 @@ def run_ours(args):
     # roofline of the advection kernel (dominant): algorithmic bytes of each
     # launch (12 B per touched node, 24 B per live particle, 17 B per
     # termination) over the measured launch durations
-    import json as _json
     peak, peak_src = hbm_peak()
     algo = algorithmic_bytes(live, nodes_touched, L)
     traffic = None if args.tile else measured_traffic(ctx.launch())
