@@ -233,6 +233,16 @@ BTO_API bto_status bto_autotune(bto_ctx *ctx, const void *const *d_field_table, 
  * autotuner times untiled shapes only (BTO_ERR_STATE while tiling is on). */
 BTO_API bto_status bto_set_tiling(bto_ctx *ctx, const int32_t tile_cells[3], int32_t threads_per_cta);
 
+/* Test hook for the bounded-wait error path of the tiled kernel: in the
+ * next `cycles` tiled cycles, CTA 0 announces on its staging barrier 16
+ * bytes more than its copies deliver, so its wait gives up after about two
+ * seconds. The CTA then waits (bounded) for its copies in flight, leaves its
+ * tiles empty and consistent (their particles are lost) and returns; the
+ * other CTAs are unaffected. bto_last_error reports BTO_ERR_TIMEOUT; the
+ * context stays usable and the next interval is reseeded as usual. Nothing
+ * faults: every wait ends by its bound. BTO_ERR_STATE unless tiling is on. */
+BTO_API bto_status bto_test_wait_timeout(bto_ctx *ctx, int32_t cycles);
+
 /* Tiling in use (host ints: tile cells x, y, z, threads per CTA, grid,
  * tiles, staging buffers per CTA, 1 if the particle records are staged with
  * the nodes; all 0 when off). */

@@ -61,6 +61,7 @@ def _declare(lib):
         "bto_get_launch": ([vp, c_i32p], ctypes.c_int),
         "bto_set_tiling": ([vp, c_i32p, ctypes.c_int32], ctypes.c_int),
         "bto_get_tiling": ([vp, c_i32p], ctypes.c_int),
+        "bto_test_wait_timeout": ([vp, ctypes.c_int32], ctypes.c_int),
         "bto_autotune": ([vp, vp, ctypes.c_int32, ctypes.c_float, vp, c_i32p, c_fp], ctypes.c_int),
         "bto_copy_active": ([vp, vp, c_i32p, vp], ctypes.c_int),
         "bto_last_error": ([vp], ctypes.c_int),
@@ -224,6 +225,10 @@ def bto_set_tiling(ctx: int, tile_cells, threads_per_cta: int = 256) -> None:
     """tile_cells = None or (0, 0, 0) switches tiling off."""
     arr = None if tile_cells is None else _arr(ctypes.c_int32, [int(v) for v in tile_cells])
     _check(load().bto_set_tiling(ctx, arr, int(threads_per_cta)), "bto_set_tiling")
+
+
+def bto_test_wait_timeout(ctx: int, cycles: int) -> None:
+    _check(load().bto_test_wait_timeout(ctx, int(cycles)), "bto_test_wait_timeout")
 
 
 def bto_get_tiling(ctx: int) -> dict:

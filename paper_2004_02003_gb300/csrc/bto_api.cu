@@ -80,6 +80,7 @@ struct bto_ctx {
     int32_t *ocnt = nullptr;        // [3] overflow counts
     float4 *tact[2] = {nullptr, nullptr};
     int32_t *derr = nullptr;        // device error flag (bounded waits)
+    int32_t inject_stall = 0;       // test hook: tiled cycles left whose first wait is made to run out
 };
 
 namespace {
@@ -569,6 +570,8 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
         a.buf_floats = c->tbuf;
         a.stage_rec = c->tstage_rec;
         a.nbuf = c->tnbuf;
+        a.inject_stall = c->inject_stall > 0 ? 1 : 0;
+        if (c->inject_stall > 0) --c->inject_stall;
         cudaError_t e = bto::launch_advect_tiled(a, c->layout, c->tnt, c->tgrid, c->tsmem, s);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -827,6 +830,14 @@ bto_status bto_set_tiling(bto_ctx *ctx, const int32_t tile_cells[3], int32_t thr
     drop_graph(ctx);
     BTO_TRY(seed(ctx, 0));
     BTO_CUDA(cudaDeviceSynchronize());
+    return BTO_OK;
+}
+
+bto_status bto_test_wait_timeout(bto_ctx *ctx, int32_t cycles) {
+    if (!ctx || cycles < 0) return BTO_ERR_INVALID_ARG;
+    if (!ctx->tiled) return BTO_ERR_STATE;
+    ctx->inject_stall = cycles;
+    drop_graph(ctx);
     return BTO_OK;
 }
 

@@ -118,6 +118,7 @@ struct TiledArgs {
     int32_t buf_floats;          // floats per staging buffer (box, then up to cap_max records)
     int32_t stage_rec;           // 1: particle records staged with the box; 0: read from the list
     int32_t nbuf;                // staging buffers (2..4)
+    int32_t inject_stall;        // test hook: CTA 0's first staging barrier never completes
 };
 
 // Kernel launchers (bto_kernels.cu). Each returns cudaGetLastError().

@@ -151,10 +151,13 @@ __device__ __forceinline__ const void *block_field(const TiledArgs &a, int b) {
     return a.field ? a.field : a.fields[b];
 }
 
-// Particles of tile t in a list with counts c: front part, then back part.
-__device__ __forceinline__ void tile_parts(const TileCounts &c, int t, int *nf, int *nm) {
-    *nf = __ldcg(c.front + t);
-    *nm = min(__ldcg(c.movein + t), __ldcg(c.lim + t));
+// Particles of tile t (bucket capacity cap) in a list with counts c: front
+// part, then back part. The counts are clamped to the bucket, so that no
+// access leaves it whatever the counts hold.
+__device__ __forceinline__ void tile_parts(const TileCounts &c, int t, int cap, int *nf, int *nm) {
+    const int f = min(max(__ldcg(c.front + t), 0), cap);
+    *nf = f;
+    *nm = min(max(min(__ldcg(c.movein + t), __ldcg(c.lim + t)), 0), cap - f);
 }
 
 
@@ -166,7 +169,7 @@ template <int LAYOUT, int NT>
 __device__ __forceinline__ void stage_tile(const TiledArgs &a, int t, float *dst, uint32_t bar) {
     const TileDev T = a.tiles[t];
     int nf, nm;
-    tile_parts(a.cin, t, &nf, &nm);
+    tile_parts(a.cin, t, T.cap, &nf, &nm);
     if (nf + nm == 0) {
         mbar_arrive(bar);
         return;
@@ -207,6 +210,9 @@ __device__ __forceinline__ void stage_tile(const TiledArgs &a, int t, float *dst
         uint32_t sdst;
         bytes += span(r, src, sdst);
     }
+    // test hook: CTA 0 announces 16 bytes that no copy delivers, so that its
+    // bounded wait runs out (the error path of bto_test_wait_timeout)
+    if (a.inject_stall && blockIdx.x == 0 && threadIdx.x == 0) bytes += 16;
     mbar_arrive_expect(bar, bytes);
     for (int r = threadIdx.x; r < ncopies; r += NT) {
         uintptr_t src;
@@ -243,9 +249,9 @@ __device__ __forceinline__ void emit_movers(const TiledArgs &a, bool mover, int 
     int q = 0;
     if (lane == leader) q = atomicAdd(a.movein_out + dest, __popc(peers));
     q = __shfl_sync(peers, q, leader) + __popc(peers & ((1u << lane) - 1u));
-    int nf, nm;
-    tile_parts(a.cin, dest, &nf, &nm);
     const int cap = __ldg(&a.tiles[dest].cap);
+    int nf, nm;
+    tile_parts(a.cin, dest, cap, &nf, &nm);
     if (q < cap - (nf + nm)) {
         __stcs(a.out + __ldg(&a.tiles[dest].base) + (cap - 1 - q), r);
     } else {
@@ -315,7 +321,7 @@ __device__ __forceinline__ void advect_tile(const TiledArgs &a, int t, const flo
 // survivor is a mover.
 template <int LAYOUT, int NT>
 __device__ void advect_overflow(const TiledArgs &a) {
-    const int64_t n = min((int64_t)__ldcg(a.ocnt_in), a.ocap);
+    const int64_t n = min(max((int64_t)__ldcg(a.ocnt_in), (int64_t)0), a.ocap);
     for (int64_t i0 = (int64_t)blockIdx.x * NT; i0 < n; i0 += (int64_t)gridDim.x * NT) {
         const int64_t i = i0 + threadIdx.x;
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -379,10 +385,16 @@ __global__ void __launch_bounds__(NT, MINB) advect_tiled_kernel(const TiledArgs 
             // them (bounded) before the CTA's shared memory is released
             for (int k = 1; k < a.nbuf && t + k * G < a.ntiles; ++k)
                 mbar_wait(full0 + 8u * ((j + k) % a.nbuf), (uint32_t)((j + k) / a.nbuf) & 1u, &no_abort, a.err);
+            // this CTA's tiles, from the current one on, are left empty and
+            // consistent (their particles are lost; the error word says so)
+            for (int t2 = t + threadIdx.x * G; t2 < a.ntiles; t2 += NT * G) {
+                a.front_out[t2] = 0;
+                a.lim_out[t2] = __ldg(&a.tiles[t2].cap);
+            }
             return;
         }
         int nf, nm;
-        tile_parts(a.cin, t, &nf, &nm);
+        tile_parts(a.cin, t, __ldg(&a.tiles[t].cap), &nf, &nm);
         float *b = tsm + (size_t)buf * a.buf_floats;
         advect_tile<LAYOUT, NT>(a, t, b, nf, nf + nm, scount, cur_b, g, s, bt, src, fw);
         __syncthreads();
@@ -424,12 +436,12 @@ __device__ __forceinline__ bool live_slot(const TileDev *__restrict__ tiles, con
         const TileDev &T = tiles[t];
         *tile = t;
         int nf, nm;
-        tile_parts(c, t, &nf, &nm);
+        tile_parts(c, t, T.cap, &nf, &nm);
         const int64_t k = i - T.base;
         return k < nf || k >= T.cap - nm;
     }
     *tile = -1;
-    return i - obase < min((int64_t)*ocnt, ocap);
+    return i - obase < min(max((int64_t)*ocnt, (int64_t)0), ocap);
 }
 
 __global__ void write_live_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t nb,

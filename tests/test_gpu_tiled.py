@@ -243,3 +243,40 @@ def test_tiling_contract():
     assert bool((out["valid"] == 1).all())
     ctx.check()
     ctx.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
+    # The test hook makes CTA 0's first staging barrier of one cycle expect
+    # 16 bytes that never arrive: its bounded wait gives up (about two
+    # seconds), the error word is raised, its tiles are left empty. The
+    # status reaches the host as BTO_ERR_TIMEOUT, and the next interval of
+    # the same context equals the untiled kernel's again.
+    import time
+    import torch
+    n, origin, h, s, L = (45, 37, 29), (-0.3, 0.7, 1.1), (0.02, 0.025, 0.03), 2, 8
+    modes = inputs.fourier_modes(7, m=16, kmax=6.0)
+    fields = [inputs.fourier_field(modes, n, origin, h, c) for c in range(L)]
+    dt = 0.3 * min(h)
+    devf = _dev(fields)
+    base = _run(n, origin, h, s, L, devf, dt)
+    ctx = bto.Context(n, origin, h, s, L)
+    ctx.set_tiling((8, 8, 8), 128)
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_test_wait_timeout(ctx.handle, -1)
+    assert e.value.status == bto.BTO_ERR_INVALID_ARG
+    bto.bto_test_wait_timeout(ctx.handle, 1)
+    t0 = time.perf_counter()
+    for f in devf:
+        ctx.advect(f, dt)
+    ctx.end_interval()
+    with pytest.raises(bto.BtoError) as e:
+        ctx.check()
+    assert e.value.status == bto.BTO_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    for f in devf:
+        ctx.advect(f, dt)
+    out = ctx.end_interval()
+    ctx.check()
+    torch.cuda.synchronize()
+    _same(base, {k: v.cpu().numpy() for k, v in out.items()})
+    ctx.close()
