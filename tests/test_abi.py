@@ -65,7 +65,16 @@ def test_null_context_calls(lib):
     assert lib.bto_end_interval(None, None, None, None, None, None) == bto.BTO_ERR_INVALID_ARG
     assert lib.bto_set_field_layout(None, 0) == bto.BTO_ERR_INVALID_ARG
     assert lib.bto_last_error(None) == bto.BTO_ERR_INVALID_ARG
+    cells = (ctypes.c_int32 * 3)(8, 8, 8)
+    assert lib.bto_set_tiling(None, cells, 256) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_get_tiling(None, (ctypes.c_int32 * 8)()) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_test_wait_timeout(None, 1) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_set_launch(None, 128, 2, 0, 0) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_get_launch(None, (ctypes.c_int32 * 5)()) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_copy_active(None, None, None, None) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_tape_backward(None, None, None, None, None) == bto.BTO_ERR_INVALID_ARG
     lib.bto_destroy(None)
+    lib.bto_tape_destroy(None)
 
 
 def test_batch_argument_checks(lib):
