@@ -11,6 +11,12 @@
 // particle's end is its last in-block position, so its gradient flows back
 // only through the cycles before its exit cycle.
 //
+// All fields of the interval are resident in the tape's table and the
+// particles are independent, so each of the forward and the reverse sweep is
+// one launch with one thread per particle (per particle and Jacobian row for
+// the Jacobian), looping over the cycles: no per-cycle launches, and the
+// adjoint stays in registers across the whole sweep.
+//
 // Reverse of x' = x + s/6 (k1 + 2 k2 + 2 k3 + k4) (cell units, s = dt/h),
 // k1 = v(x), k2 = v(x + s/2 k1), k3 = v(x + s/2 k2), k4 = v(x + s k3),
 // given lam = dL/dx':  g1 = s/6 lam, g2 = g3 = s/3 lam, g4 = s/6 lam;
@@ -36,10 +42,9 @@ struct bto_tape {
     BlockDev B{};
     int64_t P = 0;
     int32_t L = 0, K = 0, nck = 0;
-    float4 *ckpt = nullptr;     // nck * P positions (cell units) at cycles 0, K, 2K, ...
-    float4 *work[2] = {nullptr, nullptr};
-    float4 *seg = nullptr;      // K * P positions inside one segment
-    float4 *lam = nullptr;      // P adjoint (cell units)
+    float4 *ckpt = nullptr;     // nck * P positions (cell units) at cycles 0, K, 2K, ... and L
+    float4 *seg = nullptr;      // K * 3P positions inside one segment, per sweep thread
+    float4 *lam = nullptr;      // 3P adjoints (cell units): one per sweep thread
     BlockDev *d_block = nullptr;
     int32_t *exitc = nullptr;   // P exit cycle, -1 while valid
     const void *const *table = nullptr;
@@ -124,76 +129,114 @@ __global__ void tape_init_kernel(const BlockDev *__restrict__ blk, int64_t P, co
     }
 }
 
-// One forward cycle over fixed slots (no compaction). With record = true a
-// failing step records its cycle; the backward recompute passes false (the
-// exit cycles are then already known).
-__global__ void tape_step_kernel(const BlockDev *__restrict__ blk, const void *const *__restrict__ table,
-                                 int32_t c, float dt, int64_t P, const float4 *__restrict__ in,
-                                 float4 *__restrict__ out, int32_t *__restrict__ exitc, bool record) {
+// Forward over the whole interval, one thread per particle (the fields of
+// every cycle are resident in the tape's table, and particles are
+// independent): cycle after cycle, the RK4 step with the closed-box tests of
+// the advection kernel; a failing step records its cycle. Positions are kept
+// at cycles 0, K, 2K, ... (checkpoint m at cycle m K) and at L (the last
+// checkpoint).
+__global__ void tape_forward_kernel(const BlockDev *__restrict__ blk, const void *const *__restrict__ table,
+                                    int32_t L, int32_t K, float dt, int64_t P, float4 *__restrict__ ckpt,
+                                    int32_t *__restrict__ exitc) {
     const BlockDev &B = *blk;
     const Geo g = load_geo(B);
     const float3 s = make_float3(dt * B.inv_h[0], dt * B.inv_h[1], dt * B.inv_h[2]);
-    const void *field = table[c];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        float4 r = in[i];
-        const int32_t e = exitc[i];
-        if (alive_at(e, c)) {
-            float3 x = make_float3(r.x, r.y, r.z), q;
-            if (rk4_step<bto::LAYOUT_F3>(x, field, g, s, q) == 0) {
-                r.x = x.x; r.y = x.y; r.z = x.z;
-            } else if (record) {
-                exitc[i] = c;
+        float4 r = ckpt[i];
+        int32_t e = exitc[i];
+        for (int32_t c = 0; c < L; ++c) {
+            if (alive_at(e, c)) {
+                float3 x = make_float3(r.x, r.y, r.z), q;
+                if (rk4_step<bto::LAYOUT_F3>(x, table[c], g, s, q) == 0) {
+                    r.x = x.x; r.y = x.y; r.z = x.z;
+                } else {
+                    e = c;
+                }
             }
+            if ((c + 1) % K == 0 || c + 1 == L) ckpt[(size_t)((c + K) / K) * P + i] = r;
         }
-        out[i] = r;
+        exitc[i] = e;
     }
 }
 
-__global__ void tape_adj_kernel(const BlockDev *__restrict__ blk, const void *const *__restrict__ table,
-                                float *const *__restrict__ gtable, int32_t c, float dt, int64_t P,
-                                const float4 *__restrict__ xc, const int32_t *__restrict__ exitc,
-                                float4 *__restrict__ lam) {
+// Reverse of one cycle for one particle at xc (cell units) with adjoint lm
+// (see the header of this file); adds the node-velocity gradients to gF
+// when it is not NULL. Returns the adjoint before the cycle.
+__device__ __forceinline__ float3 adj_step(const float *__restrict__ f, float *__restrict__ gF, const Geo &g,
+                                           const float3 s, const float4 r, const float3 Lm) {
+    float3 k1, k2, k3, k4;
+    float J1[3][3], J2[3][3], J3[3][3], J4[3][3];
+    Stage s1, s2, s3, s4;
+    sample_jac(f, g, r.x, r.y, r.z, k1, J1, s1);
+    sample_jac(f, g, fmaf(0.5f * s.x, k1.x, r.x), fmaf(0.5f * s.y, k1.y, r.y), fmaf(0.5f * s.z, k1.z, r.z),
+               k2, J2, s2);
+    sample_jac(f, g, fmaf(0.5f * s.x, k2.x, r.x), fmaf(0.5f * s.y, k2.y, r.y), fmaf(0.5f * s.z, k2.z, r.z),
+               k3, J3, s3);
+    sample_jac(f, g, fmaf(s.x, k3.x, r.x), fmaf(s.y, k3.y, r.y), fmaf(s.z, k3.z, r.z), k4, J4, s4);
+    const float3 s6 = make_float3(s.x / 6.f, s.y / 6.f, s.z / 6.f);
+    const float3 s3v = make_float3(s.x / 3.f, s.y / 3.f, s.z / 3.f);
+    float3 g1 = make_float3(s6.x * Lm.x, s6.y * Lm.y, s6.z * Lm.z);
+    float3 g2 = make_float3(s3v.x * Lm.x, s3v.y * Lm.y, s3v.z * Lm.z);
+    float3 g3 = g2;
+    const float3 g4 = g1;
+    float3 lx = Lm;
+    float3 q = jt_times(J4, g4);
+    scatter(gF, g, s4, g4);
+    lx.x += q.x; lx.y += q.y; lx.z += q.z;
+    g3.x = fmaf(s.x, q.x, g3.x); g3.y = fmaf(s.y, q.y, g3.y); g3.z = fmaf(s.z, q.z, g3.z);
+    q = jt_times(J3, g3);
+    scatter(gF, g, s3, g3);
+    lx.x += q.x; lx.y += q.y; lx.z += q.z;
+    g2.x = fmaf(0.5f * s.x, q.x, g2.x); g2.y = fmaf(0.5f * s.y, q.y, g2.y); g2.z = fmaf(0.5f * s.z, q.z, g2.z);
+    q = jt_times(J2, g2);
+    scatter(gF, g, s2, g2);
+    lx.x += q.x; lx.y += q.y; lx.z += q.z;
+    g1.x = fmaf(0.5f * s.x, q.x, g1.x); g1.y = fmaf(0.5f * s.y, q.y, g1.y); g1.z = fmaf(0.5f * s.z, q.z, g1.z);
+    q = jt_times(J1, g1);
+    scatter(gF, g, s1, g1);
+    return make_float3(lx.x + q.x, lx.y + q.y, lx.z + q.z);
+}
+
+// One reverse sweep over the interval, one thread per (adjoint, particle):
+// thread t carries the adjoint lam[t] of particle t mod P through the
+// segments, last to first; each segment's positions are recomputed from its
+// checkpoint into the thread's own slots of seg, then the segment's cycles
+// are reversed. nthr = P for a gradient sweep, 3 P for the three rows of the
+// flow-map Jacobian (one sweep each, side by side).
+__global__ void tape_reverse_kernel(const BlockDev *__restrict__ blk, const void *const *__restrict__ table,
+                                    float *const *__restrict__ gtable, int32_t L, int32_t K, int32_t nck,
+                                    float dt, int64_t P, int64_t nthr, const float4 *__restrict__ ckpt,
+                                    float4 *__restrict__ seg, const int32_t *__restrict__ exitc,
+                                    float4 *__restrict__ lam) {
     const BlockDev &B = *blk;
     const Geo g = load_geo(B);
     const float3 s = make_float3(dt * B.inv_h[0], dt * B.inv_h[1], dt * B.inv_h[2]);
-    const float *f = reinterpret_cast<const float *>(table[c]);
-    float *gF = gtable ? gtable[c] : nullptr;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        if (!alive_at(exitc[i], c)) continue;
-        const float4 r = xc[i];
-        float3 k1, k2, k3, k4;
-        float J1[3][3], J2[3][3], J3[3][3], J4[3][3];
-        Stage s1, s2, s3, s4;
-        sample_jac(f, g, r.x, r.y, r.z, k1, J1, s1);
-        sample_jac(f, g, fmaf(0.5f * s.x, k1.x, r.x), fmaf(0.5f * s.y, k1.y, r.y), fmaf(0.5f * s.z, k1.z, r.z),
-                   k2, J2, s2);
-        sample_jac(f, g, fmaf(0.5f * s.x, k2.x, r.x), fmaf(0.5f * s.y, k2.y, r.y), fmaf(0.5f * s.z, k2.z, r.z),
-                   k3, J3, s3);
-        sample_jac(f, g, fmaf(s.x, k3.x, r.x), fmaf(s.y, k3.y, r.y), fmaf(s.z, k3.z, r.z), k4, J4, s4);
-        const float4 L4 = lam[i];
-        const float3 Lm = make_float3(L4.x, L4.y, L4.z);
-        const float3 s6 = make_float3(s.x / 6.f, s.y / 6.f, s.z / 6.f);
-        const float3 s3v = make_float3(s.x / 3.f, s.y / 3.f, s.z / 3.f);
-        float3 g1 = make_float3(s6.x * Lm.x, s6.y * Lm.y, s6.z * Lm.z);
-        float3 g2 = make_float3(s3v.x * Lm.x, s3v.y * Lm.y, s3v.z * Lm.z);
-        float3 g3 = g2;
-        const float3 g4 = g1;
-        float3 lx = Lm;
-        float3 q = jt_times(J4, g4);
-        scatter(gF, g, s4, g4);
-        lx.x += q.x; lx.y += q.y; lx.z += q.z;
-        g3.x = fmaf(s.x, q.x, g3.x); g3.y = fmaf(s.y, q.y, g3.y); g3.z = fmaf(s.z, q.z, g3.z);
-        q = jt_times(J3, g3);
-        scatter(gF, g, s3, g3);
-        lx.x += q.x; lx.y += q.y; lx.z += q.z;
-        g2.x = fmaf(0.5f * s.x, q.x, g2.x); g2.y = fmaf(0.5f * s.y, q.y, g2.y); g2.z = fmaf(0.5f * s.z, q.z, g2.z);
-        q = jt_times(J2, g2);
-        scatter(gF, g, s2, g2);
-        lx.x += q.x; lx.y += q.y; lx.z += q.z;
-        g1.x = fmaf(0.5f * s.x, q.x, g1.x); g1.y = fmaf(0.5f * s.y, q.y, g1.y); g1.z = fmaf(0.5f * s.z, q.z, g1.z);
-        q = jt_times(J1, g1);
-        scatter(gF, g, s1, g1);
-        lam[i] = make_float4(lx.x + q.x, lx.y + q.y, lx.z + q.z, 0.f);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nthr; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t % P;
+        const int32_t e = exitc[i];
+        const float4 L4 = lam[t];
+        float3 lm = make_float3(L4.x, L4.y, L4.z);
+        for (int32_t sg = nck - 2; sg >= 0; --sg) {
+            const int32_t c0 = sg * K;
+            const int32_t c1 = min(c0 + K, L);
+            float4 r = ckpt[(size_t)sg * P + i];
+            seg[t] = r;
+            for (int32_t c = c0; c + 1 < c1; ++c) {
+                if (alive_at(e, c)) {
+                    float3 x = make_float3(r.x, r.y, r.z), q;
+                    if (rk4_step<bto::LAYOUT_F3>(x, table[c], g, s, q) == 0) {
+                        r.x = x.x; r.y = x.y; r.z = x.z;
+                    }
+                }
+                seg[(size_t)(c - c0 + 1) * nthr + t] = r;
+            }
+            for (int32_t c = c1 - 1; c >= c0; --c) {
+                if (!alive_at(e, c)) continue;
+                lm = adj_step(reinterpret_cast<const float *>(table[c]), gtable ? gtable[c] : nullptr, g, s,
+                              seg[(size_t)(c - c0) * nthr + t], lm);
+            }
+        }
+        lam[t] = make_float4(lm.x, lm.y, lm.z, 0.f);
     }
 }
 
@@ -292,8 +335,6 @@ int grid_of(const bto_tape *t) {
 void free_tape(bto_tape *t) {
     if (!t) return;
     cudaFree(t->ckpt);
-    cudaFree(t->work[0]);
-    cudaFree(t->work[1]);
     cudaFree(t->seg);
     cudaFree(t->lam);
     cudaFree(t->d_block);
@@ -301,30 +342,13 @@ void free_tape(bto_tape *t) {
     delete t;
 }
 
-// One reverse sweep over the interval from the lam already initialised:
-// segments last to first, positions recomputed from each checkpoint.
-bto_status reverse_sweep(bto_tape *t, float *const *gtable, cudaStream_t s) {
-    const int grid = grid_of(t);
-    const size_t P = (size_t)t->P;
-    for (int32_t seg = t->nck - 2; seg >= 0; --seg) {
-        const int32_t c0 = seg * t->K;
-        const int32_t c1 = std::min(c0 + t->K, t->L);
-        cudaError_t e = cudaMemcpyAsync(t->seg, t->ckpt + (size_t)seg * P, sizeof(float4) * P,
-                                        cudaMemcpyDeviceToDevice, s);
-        for (int32_t c = c0; c + 1 < c1 && e == cudaSuccess; ++c) {
-            tape_step_kernel<<<grid, 256, 0, s>>>(t->d_block, t->table, c, t->dt, t->P,
-                                                  t->seg + (size_t)(c - c0) * P,
-                                                  t->seg + (size_t)(c - c0 + 1) * P, t->exitc, false);
-            e = cudaGetLastError();
-        }
-        for (int32_t c = c1 - 1; c >= c0 && e == cudaSuccess; --c) {
-            tape_adj_kernel<<<grid, 256, 0, s>>>(t->d_block, t->table, gtable, c, t->dt, t->P,
-                                                 t->seg + (size_t)(c - c0) * P, t->exitc, t->lam);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) return cuda_st(e);
-    }
-    return BTO_OK;
+// One reverse sweep of nthr adjoints (P or 3 P) from the lam already
+// initialised: a single launch.
+bto_status reverse_sweep(bto_tape *t, float *const *gtable, int64_t nthr, cudaStream_t s) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nthr + 127) / 128, (int64_t)t->sm_count * 16));
+    tape_reverse_kernel<<<grid, 128, 0, s>>>(t->d_block, t->table, gtable, t->L, t->K, t->nck, t->dt, t->P, nthr,
+                                             t->ckpt, t->seg, t->exitc, t->lam);
+    return cuda_st(cudaGetLastError());
 }
 
 }  // namespace
@@ -364,10 +388,8 @@ bto_status bto_tape_create(const int32_t extent_cells[3], const float origin[3],
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device);
     const size_t P = (size_t)num_particles;
     if (e == cudaSuccess) e = cudaMalloc(&t->ckpt, sizeof(float4) * P * (size_t)t->nck);
-    if (e == cudaSuccess) e = cudaMalloc(&t->work[0], sizeof(float4) * P);
-    if (e == cudaSuccess) e = cudaMalloc(&t->work[1], sizeof(float4) * P);
-    if (e == cudaSuccess) e = cudaMalloc(&t->seg, sizeof(float4) * P * (size_t)t->K);
-    if (e == cudaSuccess) e = cudaMalloc(&t->lam, sizeof(float4) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&t->seg, sizeof(float4) * 3 * P * (size_t)t->K);
+    if (e == cudaSuccess) e = cudaMalloc(&t->lam, sizeof(float4) * 3 * P);
     if (e == cudaSuccess) e = cudaMalloc(&t->d_block, sizeof(BlockDev));
     if (e == cudaSuccess) e = cudaMalloc(&t->exitc, sizeof(int32_t) * P);
     if (e == cudaSuccess) e = cudaMemcpy(t->d_block, &t->B, sizeof(BlockDev), cudaMemcpyHostToDevice);
@@ -397,18 +419,14 @@ bto_status bto_tape_forward(bto_tape *t, const float *d_seeds, const void *const
     t->have_forward = false;
     tape_init_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, d_seeds, t->ckpt, t->exitc);
     cudaError_t e = cudaGetLastError();
-    const float4 *cur = t->ckpt;
-    for (int32_t c = 0; c < t->L && e == cudaSuccess; ++c) {
-        // write straight into the next checkpoint slot when cycle c+1 is one
-        float4 *dst = ((c + 1) % t->K == 0 || c + 1 == t->L)
-                          ? t->ckpt + (size_t)((c + t->K) / t->K) * P
-                          : t->work[c & 1];
-        tape_step_kernel<<<grid, 256, 0, s>>>(t->d_block, d_field_table, c, dt, t->P, cur, dst, t->exitc, true);
+    if (e == cudaSuccess) {
+        const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>((t->P + 127) / 128, (int64_t)t->sm_count * 16));
+        tape_forward_kernel<<<g1, 128, 0, s>>>(t->d_block, d_field_table, t->L, t->K, dt, t->P, t->ckpt, t->exitc);
         e = cudaGetLastError();
-        cur = dst;
     }
     if (e == cudaSuccess) {
-        tape_out_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, cur, t->exitc, d_ends, d_valid, d_exit_cycle);
+        tape_out_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, t->ckpt + (size_t)(t->nck - 1) * P, t->exitc, d_ends,
+                                             d_valid, d_exit_cycle);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_st(e);
@@ -428,7 +446,7 @@ bto_status bto_tape_backward(bto_tape *t, const float *d_grad_ends, float *d_gra
     tape_lam_init_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, d_grad_ends, 0, t->lam);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_st(e);
-    const bto_status st = reverse_sweep(t, d_grad_field_table, s);
+    const bto_status st = reverse_sweep(t, d_grad_field_table, t->P, s);
     if (st != BTO_OK) return st;
     tape_lam_out_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, t->lam, d_grad_seeds, 3, 0);
     return cuda_st(cudaGetLastError());
@@ -439,15 +457,18 @@ bto_status bto_tape_jacobian(bto_tape *t, float *d_jac, bto_stream stream) {
     if (!t->have_forward) return BTO_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = grid_of(t);
+    // lam = e_axis for the three axes side by side: the sweep returns row
+    // `axis` of d end / d start in lam[axis P + i]
     for (int axis = 0; axis < 3; ++axis) {
-        // lam = e_axis: the sweep returns row `axis` of d end / d start
-        tape_lam_init_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, nullptr, axis, t->lam);
+        tape_lam_init_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, nullptr, axis, t->lam + (size_t)axis * t->P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_st(e);
-        const bto_status st = reverse_sweep(t, nullptr, s);
-        if (st != BTO_OK) return st;
-        tape_lam_out_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, t->lam, d_jac, 9, 3 * axis);
-        e = cudaGetLastError();
+    }
+    const bto_status st = reverse_sweep(t, nullptr, 3 * t->P, s);
+    if (st != BTO_OK) return st;
+    for (int axis = 0; axis < 3; ++axis) {
+        tape_lam_out_kernel<<<grid, 256, 0, s>>>(t->d_block, t->P, t->lam + (size_t)axis * t->P, d_jac, 9, 3 * axis);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_st(e);
     }
     return BTO_OK;
