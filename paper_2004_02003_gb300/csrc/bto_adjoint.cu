@@ -94,26 +94,6 @@ __device__ __forceinline__ float3 jt_times(const float (&J)[3][3], float3 gvec) 
                        J[0][2] * gvec.x + J[1][2] * gvec.y + J[2][2] * gvec.z);
 }
 
-__device__ __forceinline__ void scatter(float *__restrict__ gF, const Geo &g, const Stage &st, float3 gv) {
-    if (!gF) return;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const float w = (a ? st.fx : 1.f - st.fx) * (b ? st.fy : 1.f - st.fy) * (c ? st.fz : 1.f - st.fz);
-                const uint32_t node = (uint32_t)(st.ix + a) + g.nnx * (uint32_t)(st.iy + b) +
-                                      g.nnxy * (uint32_t)(st.iz + c);
-                float *p = gF + 3ull * node;
-                atomicAdd(p + 0, w * gv.x);
-                atomicAdd(p + 1, w * gv.y);
-                atomicAdd(p + 2, w * gv.z);
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ bool alive_at(int32_t e, int32_t c) { return e < 0 || c < e; }
 
 __global__ void tape_init_kernel(const BlockDev *__restrict__ blk, int64_t P, const float *__restrict__ seeds,
@@ -159,6 +139,53 @@ __global__ void tape_forward_kernel(const BlockDev *__restrict__ blk, const void
     }
 }
 
+// Node-velocity gradients of one reverse cycle: stage k adds w_k(corner) g_k
+// to the 8 corners of its cell. Stages whose points lie in the same cell are
+// summed per corner first, so that each distinct cell takes 24 atomic adds
+// (the stages of a step mostly share a cell).
+__device__ __forceinline__ float stage_w(const Stage &st, int a, int b, int c) {
+    return (a ? st.fx : 1.f - st.fx) * (b ? st.fy : 1.f - st.fy) * (c ? st.fz : 1.f - st.fz);
+}
+
+__device__ __forceinline__ void scatter_step(float *__restrict__ gF, const Geo &g, const Stage (&st)[4],
+                                             const float3 (&gs)[4]) {
+    if (!gF) return;
+    unsigned done = 0;
+#pragma unroll
+    for (int k = 3; k >= 0; --k) {
+        if (done & (1u << k)) continue;
+        bool in[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            in[j] = j <= k && !(done & (1u << j)) && st[j].ix == st[k].ix && st[j].iy == st[k].iy &&
+                    st[j].iz == st[k].iz;
+            if (in[j]) done |= 1u << j;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    float vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+                    for (int j = 3; j >= 0; --j) {
+                        if (!in[j]) continue;
+                        const float w = stage_w(st[j], a, b, c);
+                        vx = fmaf(w, gs[j].x, vx);
+                        vy = fmaf(w, gs[j].y, vy);
+                        vz = fmaf(w, gs[j].z, vz);
+                    }
+                    const uint32_t node = (uint32_t)(st[k].ix + a) + g.nnx * (uint32_t)(st[k].iy + b) +
+                                          g.nnxy * (uint32_t)(st[k].iz + c);
+                    float *p = gF + 3ull * node;
+                    atomicAdd(p + 0, vx);
+                    atomicAdd(p + 1, vy);
+                    atomicAdd(p + 2, vz);
+                }
+    }
+}
+
 // Reverse of one cycle for one particle at xc (cell units) with adjoint lm
 // (see the header of this file); adds the node-velocity gradients to gF
 // when it is not NULL. Returns the adjoint before the cycle.
@@ -166,34 +193,34 @@ __device__ __forceinline__ float3 adj_step(const float *__restrict__ f, float *_
                                            const float3 s, const float4 r, const float3 Lm) {
     float3 k1, k2, k3, k4;
     float J1[3][3], J2[3][3], J3[3][3], J4[3][3];
-    Stage s1, s2, s3, s4;
-    sample_jac(f, g, r.x, r.y, r.z, k1, J1, s1);
+    Stage st[4];
+    sample_jac(f, g, r.x, r.y, r.z, k1, J1, st[0]);
     sample_jac(f, g, fmaf(0.5f * s.x, k1.x, r.x), fmaf(0.5f * s.y, k1.y, r.y), fmaf(0.5f * s.z, k1.z, r.z),
-               k2, J2, s2);
+               k2, J2, st[1]);
     sample_jac(f, g, fmaf(0.5f * s.x, k2.x, r.x), fmaf(0.5f * s.y, k2.y, r.y), fmaf(0.5f * s.z, k2.z, r.z),
-               k3, J3, s3);
-    sample_jac(f, g, fmaf(s.x, k3.x, r.x), fmaf(s.y, k3.y, r.y), fmaf(s.z, k3.z, r.z), k4, J4, s4);
+               k3, J3, st[2]);
+    sample_jac(f, g, fmaf(s.x, k3.x, r.x), fmaf(s.y, k3.y, r.y), fmaf(s.z, k3.z, r.z), k4, J4, st[3]);
     const float3 s6 = make_float3(s.x / 6.f, s.y / 6.f, s.z / 6.f);
     const float3 s3v = make_float3(s.x / 3.f, s.y / 3.f, s.z / 3.f);
-    float3 g1 = make_float3(s6.x * Lm.x, s6.y * Lm.y, s6.z * Lm.z);
-    float3 g2 = make_float3(s3v.x * Lm.x, s3v.y * Lm.y, s3v.z * Lm.z);
-    float3 g3 = g2;
-    const float3 g4 = g1;
+    float3 gs[4];
+    gs[0] = make_float3(s6.x * Lm.x, s6.y * Lm.y, s6.z * Lm.z);
+    gs[1] = make_float3(s3v.x * Lm.x, s3v.y * Lm.y, s3v.z * Lm.z);
+    gs[2] = gs[1];
+    gs[3] = gs[0];
     float3 lx = Lm;
-    float3 q = jt_times(J4, g4);
-    scatter(gF, g, s4, g4);
+    float3 q = jt_times(J4, gs[3]);
     lx.x += q.x; lx.y += q.y; lx.z += q.z;
-    g3.x = fmaf(s.x, q.x, g3.x); g3.y = fmaf(s.y, q.y, g3.y); g3.z = fmaf(s.z, q.z, g3.z);
-    q = jt_times(J3, g3);
-    scatter(gF, g, s3, g3);
+    gs[2].x = fmaf(s.x, q.x, gs[2].x); gs[2].y = fmaf(s.y, q.y, gs[2].y); gs[2].z = fmaf(s.z, q.z, gs[2].z);
+    q = jt_times(J3, gs[2]);
     lx.x += q.x; lx.y += q.y; lx.z += q.z;
-    g2.x = fmaf(0.5f * s.x, q.x, g2.x); g2.y = fmaf(0.5f * s.y, q.y, g2.y); g2.z = fmaf(0.5f * s.z, q.z, g2.z);
-    q = jt_times(J2, g2);
-    scatter(gF, g, s2, g2);
+    gs[1].x = fmaf(0.5f * s.x, q.x, gs[1].x); gs[1].y = fmaf(0.5f * s.y, q.y, gs[1].y);
+    gs[1].z = fmaf(0.5f * s.z, q.z, gs[1].z);
+    q = jt_times(J2, gs[1]);
     lx.x += q.x; lx.y += q.y; lx.z += q.z;
-    g1.x = fmaf(0.5f * s.x, q.x, g1.x); g1.y = fmaf(0.5f * s.y, q.y, g1.y); g1.z = fmaf(0.5f * s.z, q.z, g1.z);
-    q = jt_times(J1, g1);
-    scatter(gF, g, s1, g1);
+    gs[0].x = fmaf(0.5f * s.x, q.x, gs[0].x); gs[0].y = fmaf(0.5f * s.y, q.y, gs[0].y);
+    gs[0].z = fmaf(0.5f * s.z, q.z, gs[0].z);
+    q = jt_times(J1, gs[0]);
+    scatter_step(gF, g, st, gs);
     return make_float3(lx.x + q.x, lx.y + q.y, lx.z + q.z);
 }
 
