@@ -505,13 +505,14 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     for _ in range(max(1, args.warmup)):
         plain_step()
     torch.cuda.synchronize()
+    barrier(world)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
         plain_step()
     t1.record(stream)
     torch.cuda.synchronize()
-    res["plain_value"] = psteps * args.steps / (t0.elapsed_time(t1) / 1e3)
+    res["plain_value"] = aggregate(psteps * args.steps, t0.elapsed_time(t1) / 1e3, world)[2]
     for p in plain:
         p.check(); p.close()
 
@@ -524,6 +525,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
         g.interval_graph(table, dt)
         g.end_interval(gout)
     torch.cuda.synchronize()
+    barrier(world)
     t0.record(stream)
     for _ in range(args.steps):
         g.interval_graph(table, dt)
@@ -532,7 +534,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     torch.cuda.synchronize()
     g.check()
     assert np.array_equal(gout["exit_cycle"].cpu().numpy(), exit_ref)
-    res["graph_value"] = psteps * args.steps / (t0.elapsed_time(t1) / 1e3)
+    res["graph_value"] = aggregate(psteps * args.steps, t0.elapsed_time(t1) / 1e3, world)[2]
     g.close()
 
     # (3) accuracy cost vs the global flow map (rank 0, untimed)
@@ -584,7 +586,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     # (5) end to end: fields copied from pinned host memory every cycle,
     # basis flows copied back every interval; copies overlap compute on a
     # second stream with a two-slot device ring.
-    res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb)
+    res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb, world)
     return res
 
 
@@ -998,7 +1000,7 @@ def large_leg(args, dev, stream):
             "pathlines_vs_rk4_ground_truth": path_err}
 
 
-def e2e(args, ctx, fields, dt, dev, stream, nb):
+def e2e(args, ctx, fields, dt, dev, stream, nb, world=1):
     import torch
     L = INTERVAL
     R = 8  # pinned host ring of per-cycle fields (cycle c uses host[c % R])
@@ -1062,10 +1064,13 @@ def e2e(args, ctx, fields, dt, dev, stream, nb):
         return units
 
     run(max(1, args.warmup))
+    barrier(world)
     t = time.perf_counter()
     units = run(args.steps)
     el = time.perf_counter() - t
-    return {"value": units / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
+    # whole job: all ranks' units over the slowest rank's time
+    _, _, value = aggregate(units, el, world)
+    return {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
             "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R, "copy_streams": K}
 
 
