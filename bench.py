@@ -579,9 +579,9 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     if rank == 0:
         res["tiled_ablation"] = tiled_leg(args, ext, org, spc, table, dt, out, dev, stream)
         res["adjoint"] = adjoint_leg(args, dev, stream)
-        res["batched"] = batched_leg(args, dev, stream)
-        if not args.no_large:
-            res["large"] = large_leg(args, dev, stream)
+    res["batched"] = batched_leg(args, dev, stream, rank, world)
+    if rank == 0 and not args.no_large:
+        res["large"] = large_leg(args, dev, stream)
 
     # (5) end to end: fields copied from pinned host memory every cycle,
     # basis flows copied back every interval; copies overlap compute on a
@@ -707,17 +707,34 @@ def tiled_leg(args, ext, org, spc, table, dt, ref_out, dev, stream,
     return rows
 
 
-def batched_leg(args, dev, stream):
+def batched_leg(args, dev, stream, rank=0, world=1):
     """Batched workload: 512 uneven blocks in one persistent launch per cycle
     (and as one CUDA graph per interval) against 512 single-block contexts,
-    after the native autotuner has picked the launch shape."""
+    after the native autotuner has picked the launch shape. Under several
+    ranks each rank takes its share of the 512 blocks (whole blocks, by
+    estimated work) and the values are whole-job figures (strong scaling of
+    this fixed workload)."""
     import torch
     from paper_2004_02003_gb300 import bto, inputs
-    ext, org, spc, strides = batched_layout()
-    nb, L, NF = len(ext), 64, 4
+    from paper_2004_02003_gb300.partition import block_work, partition_blocks
+    ext_all, org_all, spc_all, strides_all = batched_layout()
+    L, NF = 64, 4
+    parts = partition_blocks(block_work(ext_all, strides_all, L), world)
+    mine = parts[rank]
+    ext = [ext_all[b] for b in mine]
+    org = [org_all[b] for b in mine]
+    spc = [spc_all[b] for b in mine]
+    strides = [strides_all[b] for b in mine]
+    nb = len(ext)
     modes = inputs.fourier_modes(SEED + 2, m=32, kmin=1.0, kmax=16.0, drift_max=0.05)
     vmax = np.pi * inputs.DG_A * 1.5 + 0.1      # bound of |u| (gyre + scaled turbulence)
-    dt = 0.25 * min(min(h) for h in spc) / vmax
+    dt = 0.25 * min(min(h) for h in spc_all) / vmax
+    if nb == 0:      # more ranks than blocks: take part in the collectives only
+        for _ in range(3):
+            barrier(world)
+        for _ in range(3):
+            aggregate(0, 0.0, world)
+        return None
     fields = [[inputs.double_gyre_fourier_torch(modes, ext[b], org[b], spc[b], c * dt, c, dev)
                for b in range(nb)] for c in range(NF)]
     table = torch.tensor([fields[c % NF][b].data_ptr() for c in range(L) for b in range(nb)],
@@ -749,9 +766,11 @@ def batched_leg(args, dev, stream):
         return e0.elapsed_time(e1) / reps
 
     reps = max(3, min(args.steps, 10))
+    barrier(world)
     t_b = timed(run_batched, reps)
     ex = out["exit_cycle"].cpu().numpy()
     psteps = count_particle_steps(ex, L)
+    barrier(world)
     t_g = timed(run_graph, reps)
     ctx.check()
     plain = [bto.Context(ext[b], org[b], spc[b], strides[b], L) for b in range(nb)]
@@ -764,11 +783,16 @@ def batched_leg(args, dev, stream):
         for b in range(nb):
             plain[b].end_interval(pouts[b])
 
+    barrier(world)
     t_p = timed(run_plain, 1, warm=1)
     for p in plain:
         p.check()
         p.close()
     P = ctx.P
+    # whole-job values: all ranks' particle-steps over the slowest rank's time
+    v_b = aggregate(psteps, t_b / 1e3, world)[2]
+    v_g = aggregate(psteps, t_g / 1e3, world)[2]
+    v_p = aggregate(psteps, t_p / 1e3, world)[2]
     # roofline of the batched launch: algorithmic bytes (12 per node of the
     # cells holding a live particle, 24 per live particle, 17 per
     # termination) over the advect-only time of one interval; the touched
@@ -795,8 +819,8 @@ def batched_leg(args, dev, stream):
     return {"workload": "512 uneven blocks (16..96 cells per axis, aspect <= 3), strides {1,2,4}, "
                         "double gyre + 32 Fourier modes, interval 64",
             "blocks": nb, "particles": P, "nodes": nodes, "dt": dt, "autotune": tune,
-            "batched_value": psteps / (t_b / 1e3), "graph_value": psteps / (t_g / 1e3),
-            "plain_value": psteps / (t_p / 1e3), "batched_vs_plain": t_p / t_b,
+            "ranks": world, "blocks_per_rank": [len(p) for p in parts],
+            "batched_value": v_b, "graph_value": v_g, "plain_value": v_p, "batched_vs_plain": v_b / v_p,
             "ms_per_interval": {"batched": t_b, "graph": t_g, "plain": t_p},
             "terminated_frac": float((ex >= 0).mean()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
