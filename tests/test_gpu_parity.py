@@ -556,3 +556,74 @@ def test_stitching_matches_oracle():
     ok = ~np.isnan(ref)
     assert np.isnan(ref).any() and ok.any()
     assert np.max(np.abs(g[ok] - ref[ok])) < 1e-5
+
+
+def test_batched_f4_graph_and_exits_equal_f3_per_cycle():
+    # The batched form with F4 fields through the interval graph, with exit
+    # locations, equals the batched F3 form driven cycle by cycle.
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt = 10, 0.006
+    nb = len(ext)
+    modes = inputs.fourier_modes(13, m=12, kmax=5.0)
+    f3 = [[inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(nb)] for c in range(L)]
+    dev3 = [_dev(fc) for fc in f3]
+    dev4 = [_dev([to_f4(f) for f in fc]) for fc in f3]
+    t3 = torch.tensor([t.data_ptr() for fc in dev3 for t in fc], dtype=torch.int64, device="cuda")
+    t4 = torch.tensor([t.data_ptr() for fc in dev4 for t in fc], dtype=torch.int64, device="cuda")
+    a = bto.Context.batch(ext, origins, spac, strides, L)
+    for c in range(L):
+        a.advect_batch(t3[c * nb:(c + 1) * nb], dt)
+    ra = {k: v.cpu().numpy() for k, v in a.end_interval(exits=True).items()}
+    b = bto.Context.batch(ext, origins, spac, strides, L)
+    b.set_layout(bto.BTO_FIELD_F4_AOS)
+    b.interval_graph(t4, dt)
+    rb = {k: v.cpu().numpy() for k, v in b.end_interval(exits=True).items()}
+    a.check(); b.check()
+    for k in ra:
+        assert np.array_equal(ra[k], rb[k], equal_nan=True), k
+    assert (ra["valid"] == 0).any() and np.isfinite(ra["exit_pos"][ra["valid"] == 0]).all()
+    a.close(); b.close()
+
+
+def test_copy_active_lists_the_live_particles_of_each_block():
+    # After c cycles the active list holds, per block, exactly the particles
+    # whose exit cycle (from the finished interval) is -1 or >= c, each once,
+    # at the positions the same interval reaches after c cycles.
+    import torch
+    ext, origins, spac, strides = _uneven_blocks()
+    L, dt, stop = 12, 0.006, 7
+    nb = len(ext)
+    modes = inputs.fourier_modes(14, m=12, kmax=5.0)
+    devf = [_dev([inputs.fourier_field(modes, ext[b], origins[b], spac[b], c) for b in range(nb)]) for c in range(L)]
+    table = torch.tensor([t.data_ptr() for fc in devf for t in fc], dtype=torch.int64, device="cuda")
+    full = bto.Context.batch(ext, origins, spac, strides, L)
+    for c in range(L):
+        full.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    ref = {k: v.cpu().numpy() for k, v in full.end_interval().items()}
+    full.close()
+    part = bto.Context.batch(ext, origins, spac, strides, stop)
+    for c in range(stop):
+        part.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    at_stop = {k: v.cpu().numpy() for k, v in part.end_interval().items()}
+    # rerun the first `stop` cycles and read the list before the writer
+    for c in range(stop):
+        part.advect_batch(table[c * nb:(c + 1) * nb], dt)
+    act = torch.empty((part.P, 4), dtype=torch.float32, device="cuda")
+    live = part.copy_active(act)
+    off = part.offsets()
+    act = act.cpu().numpy()
+    for blk in range(nb):
+        ids = act[off[blk]:off[blk] + live[blk], 3].view(np.int32)
+        e = ref["exit_cycle"][off[blk]:off[blk + 1]]
+        want = np.flatnonzero((e < 0) | (e >= stop))
+        assert np.array_equal(np.sort(ids), want), blk
+        assert len(np.unique(ids)) == len(ids)
+        # xi of the listed particles = the ends of the stop-cycle interval
+        xi = act[off[blk]:off[blk] + live[blk], :3].astype(np.float64)
+        phys = np.asarray(origins[blk]) + xi * np.asarray(spac[blk])
+        ends = at_stop["ends"][off[blk]:off[blk + 1]][ids]
+        assert np.max(np.abs(phys - ends) / np.asarray(spac[blk])) < 1e-4
+    part.end_interval()
+    part.check()
+    part.close()
