@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--ingest", action="store_true", help="repack F3 fields to 16-byte nodes per block (H1)")
     ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
     ap.add_argument("--e2e-streams", type=int, default=4, help="copy streams of the end-to-end leg")
+    ap.add_argument("--only", default="", choices=["", "batched"],
+                    help="run one workload leg alone and print its JSON (for profiling)")
+    ap.add_argument("--no-plain", action="store_true", help="batched leg: skip the 512-context plain comparison")
     ap.add_argument("--tile", default="", help="tx,ty,tz[,threads]: tiled advection kernel (default: off)")
     ap.add_argument("--fields", type=int, default=INTERVAL,
                     help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
@@ -718,7 +721,7 @@ def batched_leg(args, dev, stream, rank=0, world=1):
     from paper_2004_02003_gb300 import bto, inputs
     from paper_2004_02003_gb300.partition import block_work, partition_blocks
     ext_all, org_all, spc_all, strides_all = batched_layout()
-    L, NF = 64, 4
+    L, NF = 64, max(1, min(4, args.fields))
     parts = partition_blocks(block_work(ext_all, strides_all, L), world)
     mine = parts[rank]
     ext = [ext_all[b] for b in mine]
@@ -773,7 +776,7 @@ def batched_leg(args, dev, stream, rank=0, world=1):
     barrier(world)
     t_g = timed(run_graph, reps)
     ctx.check()
-    plain = [bto.Context(ext[b], org[b], spc[b], strides[b], L) for b in range(nb)]
+    plain = [] if args.no_plain else [bto.Context(ext[b], org[b], spc[b], strides[b], L) for b in range(nb)]
     pouts = [p.alloc_outputs(dev) for p in plain]
 
     def run_plain():
@@ -784,7 +787,7 @@ def batched_leg(args, dev, stream, rank=0, world=1):
             plain[b].end_interval(pouts[b])
 
     barrier(world)
-    t_p = timed(run_plain, 1, warm=1)
+    t_p = timed(run_plain, 1, warm=1) if not args.no_plain else float("nan")
     for p in plain:
         p.check()
         p.close()
@@ -1209,10 +1212,27 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_only(args):
+    """One workload leg alone on one GPU (its own JSON line, not the
+    benchmark's): a short command to capture that leg's kernels."""
+    import torch
+    from paper_2004_02003_gb300 import bto
+    from paper_2004_02003_gb300 import build as lib_build
+    lib_build.build()
+    bto.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if args.only == "batched":
+        print(json.dumps({"leg": "batched", "result": batched_leg(args, dev, stream)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 
