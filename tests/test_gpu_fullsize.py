@@ -198,3 +198,51 @@ def test_large_full_size_sampled_parity(cuda_device):
     far = d > reach + 1e-9
     assert int(far.sum().item()) > 50000000
     assert bool((out["valid"][far] == 1).all())
+
+
+def test_largest_block_uses_64_bit_offsets(cuda_device):
+    """The largest block the library accepts: 800^3 cells, 801^3 = 513,922,401
+    nodes (limit 2^29), a 6.2 GB F3 field whose byte offsets exceed 2^32.
+    An affine field u = A x + b is interpolated exactly, so every particle
+    whose whole path stays inside follows the RK4 closed form; both the
+    untiled and the tiled kernel are checked."""
+    import torch
+    from paper_2004_02003_gb300 import build
+    build.build()
+    n, s, L, dt = 800, 16, 3, 0.5
+    h = (1.0, 1.0, 1.0)
+    A = np.array([[-0.02, 0.05, 0.0], [-0.05, -0.02, 0.01], [0.0, -0.01, 0.03]])
+    c = np.array([400.0, 400.0, 400.0])
+    bvec = -A @ c
+    ax = torch.arange(n + 1, dtype=torch.float32, device=cuda_device)
+    f = torch.empty((n + 1, n + 1, n + 1, 3), dtype=torch.float32, device=cuda_device)
+    for comp in range(3):
+        # u_comp = A[comp] . (x, y, z) + b[comp], x fastest; built plane by plane
+        for zi in range(0, n + 1, 100):
+            z = ax[zi:zi + 100].view(-1, 1, 1)
+            f[zi:zi + 100, :, :, comp] = (A[comp, 0] * ax.view(1, 1, -1) + A[comp, 1] * ax.view(1, -1, 1)
+                                          + A[comp, 2] * z + bvec[comp])
+    Z = dt * A
+    R = np.eye(3) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    for tile in (None, (16, 16, 16)):
+        ctx = bto.Context((n, n, n), (0, 0, 0), h, s, L)
+        if tile:
+            ctx.set_tiling(tile, 256)
+        for _ in range(L):
+            ctx.advect(f, dt)
+        out = ctx.end_interval()
+        ctx.check()
+        torch.cuda.synchronize()
+        seeds = out["seeds"].cpu().numpy().astype(np.float64)
+        ends = out["ends"].cpu().numpy().astype(np.float64)
+        valid = out["valid"].cpu().numpy()
+        x = seeds.copy()
+        inside = np.ones(len(x), dtype=bool)
+        for _ in range(L):
+            x = c + (x - c) @ R.T
+            inside &= np.all((x > 40.0) & (x < n - 40.0), axis=1)   # stage points within ~21 cells
+        assert ctx.P == 50 ** 3 and inside.sum() > 50000
+        assert np.all(valid[inside] == 1)
+        assert np.max(np.abs(ends[inside] - x[inside])) < 2e-3      # cells; FP32 at |x| ~ 800
+        ctx.close()
+    del f
