@@ -280,3 +280,19 @@ def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
     torch.cuda.synchronize()
     _same(base, {k: v.cpu().numpy() for k, v in out.items()})
     ctx.close()
+
+
+def test_every_particle_leaves_in_the_first_cycle_then_empty_lists():
+    # u = (+40, 0, 0) cells per unit time with dt = 1 on a 16^3 block: every
+    # stage point p2 lies 20 cells further in x, outside, so every particle
+    # terminates in cycle 0 at its seed; the remaining cycles run on empty
+    # lists (untiled and tiled).
+    n, h, L, dt = (16, 16, 16), (1.0, 1.0, 1.0), 5, 1.0
+    f = inputs.uniform_field(n, (40.0, 0.0, 0.0))
+    devf = _dev([f] * L)
+    for tile in (None, (4, 4, 4)):
+        g = _run(n, (0, 0, 0), h, 2, L, devf, dt, tile=tile, exits=True)
+        assert np.all(g["valid"] == 0) and np.all(g["exit_cycle"] == 0)
+        assert np.array_equal(g["ends"], g["seeds"])
+        # the clipped exit point lies on the +x face, at time 1/2 * t
+        assert np.allclose(g["exit_pos"][:, 0], 16.0) and np.all(g["exit_time"] <= 0.5)
