@@ -87,6 +87,36 @@ def test_turb256_full_size_sampled_parity(cuda_device):
         assert np.all(gpu["valid"][off[b]:off[b + 1]][far] == 1)
     assert 0.01 < 1.0 - gpu["valid"].mean() < 0.5
 
+    # Eq. (hx), second part: on the global seed lattice (the blocks' lattices
+    # side by side), take the lines along one axis whose other two
+    # coordinates lie farther than the largest displacement from every face
+    # normal to those axes. Particles on such a line can only leave through
+    # faces normal to the line, so missing basis flows come in runs around
+    # those faces, and two valid neighbours across a run are at most
+    # 2 h_x + 2 (largest displacement) apart, h_x the seed spacing: in
+    # lattice units, 2 + 2 reach / h_x. (Lines parallel to a face, within
+    # reach of it, may miss every flow; the bound is across faces.)
+    S = n // bench.STRIDE
+    GS = G // bench.STRIDE
+    lat = np.zeros((GS, GS, GS), dtype=np.uint8)          # (z, y, x)
+    for b, (bx, by, bz) in enumerate(blocks):
+        lat[bz * S:(bz + 1) * S, by * S:(by + 1) * S, bx * S:(bx + 1) * S] = \
+            gpu["valid"][off[b]:off[b + 1]].reshape(S, S, S)
+    hx = bench.STRIDE * h
+    j = np.arange(GS) % S
+    far_idx = np.minimum(j, S - j) * hx > reach + 1e-9
+    cross = far_idx[:, None] & far_idx[None, :]
+    bound = 2.0 + 2.0 * reach / hx
+    widest = 0
+    for axis in range(3):
+        lines = np.moveaxis(lat, axis, -1)[cross]          # (lines, GS)
+        assert lines.shape[0] > 0
+        for line in lines[np.any(lines == 0, axis=1)]:
+            ok = np.flatnonzero(line == 1)
+            if ok.size >= 2:
+                widest = max(widest, int(np.diff(ok).max()))
+    assert 1 < widest <= bound, (widest, bound)
+
 
 def test_batched512_full_size_sampled_parity(cuda_device):
     """The batched workload (512 uneven blocks, strides 1/2/4, double gyre +
