@@ -395,7 +395,7 @@ BTO_API void bto_tape_destroy(bto_tape *tape);
  *   d_seeds, d_ends, d_valid, d_exit_cycle
  *                  outputs as in bto_end_interval (d_exit_cycle may be NULL)
  *   stream         all work is enqueued on it; the call does not wait
- * Seeds are processed in canonical lattice order (not Morton order); the
+ * Seeds are processed in canonical lattice order (not brick order); the
  * outputs are identical to the context calls'. */
 #define BTO_NOALLOC_MAX_SEEDS 65536
 #define BTO_NOALLOC_SCRATCH_BYTES 3432704

@@ -2,7 +2,7 @@
 //
 // A context owns, on one device:
 //   blocks   [nb] BlockDev          geometry of each block
-//   perm     [P] int32              lattice point of each Morton rank, per block
+//   perm     [P] int32              lattice point of each rank in brick order, per block
 //   gblock   [slots/32] int32       block of each 32-slot unit of the lists
 //   act[2]   [slots] float4         active lists (ping-pong): xi (cell units), id bits
 //   gcnt[2]  [slots/32] int32       live particles per group (ping-pong)
@@ -127,6 +127,34 @@ void morton_order(const int32_t S[3], int32_t *out) {
         const uint32_t x = compact3(code), y = compact3(code >> 1), z = compact3(code >> 2);
         if ((int32_t)x < S[0] && (int32_t)y < S[1] && (int32_t)z < S[2])
             out[k++] = (int32_t)x + S[0] * ((int32_t)y + S[1] * (int32_t)z);
+    }
+}
+
+// Canonical lattice ids in brick order: the lattice is cut into bricks of
+// bx x by x bz seeds (32 seeds: bx = min(32, Sx rounded up to a power of
+// two), then by, then bz), the bricks are taken in Morton order and the
+// seeds of a brick x fastest. A warp then holds one run of 32 seeds along x
+// where the block is that wide, so each of its corner loads touches the
+// node rows of a few cell rows instead of the eight rows of a 4 x 4 x 2
+// Morton cube: about 13% more particle-steps per second on 128^3 blocks at
+// seed stride 2 and 12% on the uneven batched blocks, measured against
+// plain Morton order (bricks 32 x 1 x 1, 16 x 2 x 1, 8 x 4 x 1, 8 x 2 x 2,
+// 64 x 1 x 1 and 32 x 2 x 1 were measured; long x runs win).
+void brick_order(const int32_t S[3], int32_t *out) {
+    auto pow2 = [](int32_t v) { int32_t r = 1; while (r < v) r <<= 1; return r; };
+    const int32_t bx = std::min(32, pow2(S[0]));
+    const int32_t by = std::min(32 / bx, pow2(S[1]));
+    const int32_t bz = std::max(1, 32 / (bx * by));
+    const int32_t B[3] = {(S[0] + bx - 1) / bx, (S[1] + by - 1) / by, (S[2] + bz - 1) / bz};
+    std::vector<int32_t> bricks((size_t)B[0] * B[1] * B[2]);
+    morton_order(B, bricks.data());
+    int64_t k = 0;
+    for (const int32_t q : bricks) {
+        const int32_t qx = q % B[0], qy = (q / B[0]) % B[1], qz = q / (B[0] * B[1]);
+        for (int32_t z = qz * bz; z < std::min(S[2], (qz + 1) * bz); ++z)
+            for (int32_t y = qy * by; y < std::min(S[1], (qy + 1) * by); ++y)
+                for (int32_t x = qx * bx; x < std::min(S[0], (qx + 1) * bx); ++x)
+                    out[k++] = x + S[0] * (y + S[1] * z);
     }
 }
 
@@ -446,7 +474,7 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     if (e != cudaSuccess) { (void)cudaGetLastError(); free_ctx(c); return cuda_status(e); }
 
     std::vector<int32_t> perm((size_t)P);
-    for (int32_t b = 0; b < nb; ++b) morton_order(bl[(size_t)b].S, perm.data() + bl[(size_t)b].base);
+    for (int32_t b = 0; b < nb; ++b) brick_order(bl[(size_t)b].S, perm.data() + bl[(size_t)b].base);
 
     const size_t units = (size_t)(slots / bto::kUnit);
     e = cudaMalloc(&c->blocks, sizeof(BlockDev) * (size_t)nb);

@@ -32,7 +32,7 @@ constexpr int kUnit = 32;
 
 // Arguments of one advection cycle (kernel K3: RK4 + termination + compaction).
 // The active list is cut into groups of G = 32 * ppt slots; group g holds
-// gcnt[g] live particles in its first slots, in Morton order of their seeds.
+// gcnt[g] live particles in its first slots, in brick order of their seeds.
 struct AdvectArgs {
     const BlockDev *blocks;      // [nb] device
     const int32_t *gblock;       // [slots / 32] block of each 32-slot unit

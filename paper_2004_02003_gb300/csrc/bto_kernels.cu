@@ -1,6 +1,6 @@
 // libbto kernels for sm_103a.
 //
-//   K2 seed_kernel        lattice seeds in Morton order (Sec. 2.3)
+//   K2 seed_kernel        lattice seeds in brick order (Sec. 2.3)
 //   K3 advect_kernel      one RK4 step per live particle with trilinear
 //                         sampling (Sec. 3.1, Eq. 1), closed-box termination
 //                         of stage and end points (Sec. 3.1, Sec. 3.3), and
@@ -12,9 +12,10 @@
 //
 // Design (GB300): the hot kernel is a gather over the velocity nodes, bound
 // by memory traffic, not by arithmetic; there is no dense contraction, so the
-// tensor cores are not used. Particles are stored in Morton order of their
-// seeds so that neighbouring threads touch neighbouring cells (L1/L2 reuse
-// of each node); the 8 corners of a cell stay in registers across the four
+// tensor cores are not used. Particles are stored in brick order of their
+// seeds (runs of 32 seeds along x, the runs in Morton order) so that the
+// lanes of a warp touch few node rows and neighbouring warps neighbouring
+// rows (L1/L2 reuse of each node); the 8 corners of a cell stay in registers across the four
 // RK4 stages and are reloaded only when a stage point lands in another cell;
 // each warp owns groups of 32*PPT particles and compacts the survivors of a
 // group inside that group (ballot/popc, no barrier, no atomic); the grid is
@@ -48,7 +49,7 @@ __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, i
 // particles (PPT rounds of 32) and writes the survivors, in order, to the
 // front of the same group in the output list. Warps take groups g, g + W,
 // g + 2W, ... (W = warps in the grid), so the groups in flight at any time
-// are neighbours in Morton order. There is no barrier and no atomic: a
+// are neighbours in brick order. There is no barrier and no atomic: a
 // terminated particle only leaves the group's live prefix.
 // ---------------------------------------------------------------------------
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
 
 // ---------------------------------------------------------------------------
 // K2: seeds. Slot i of block b's region holds the lattice point perm[base + m]
-// (m = i - slot_base; Morton order of the lattice); positions are the exact
+// (m = i - slot_base; brick order of the lattice); positions are the exact
 // integers j*s in cell units. Also sets every group's live count.
 // ---------------------------------------------------------------------------
 __global__ void seed_kernel(const BlockDev *__restrict__ blocks, const int32_t *__restrict__ gblock,

@@ -390,7 +390,7 @@ def test_field_base_alignment_does_not_change_results(abc_case, layout, offset_f
 
 def test_last_node_pairs_near_array_end():
     # Particles in the cells at the far corner read the last nodes of the
-    # field (the F3 vector path must switch to scalar loads there).
+    # field: an F3 gather with wide loads must not read past them.
     n, h, L, dt = (9, 7, 5), (0.1, 0.1, 0.1), 6, 0.02
     f = np.zeros((6, 8, 10, 3), dtype=np.float32)
     f[..., 0] = -0.5
