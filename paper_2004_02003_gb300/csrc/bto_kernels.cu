@@ -54,6 +54,12 @@ __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, i
 // ---------------------------------------------------------------------------
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
+    // Programmatic dependent launch: the grid may be scheduled while the
+    // previous cycle's grid drains; it reads nothing before that grid has
+    // completed and its writes are visible (a no-op when launched without
+    // the dependency). Then the next cycle's grid may be scheduled.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int G = 32 * PPT;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -348,10 +354,21 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
     }
 }
 
+// Each cycle's grid is launched with programmatic stream serialisation, so
+// its launch and CTA set-up overlap the previous cycle's tail.
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 cudaError_t launch_t(const AdvectArgs &a, int grid, size_t dyn, cudaStream_t s) {
-    advect_kernel<LAYOUT, NT, PPT, BATCHED, MINB><<<grid, NT, dyn, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, advect_kernel<LAYOUT, NT, PPT, BATCHED, MINB>, a);
 }
 
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
