@@ -306,8 +306,8 @@ def kernel_source_sha256():
 
 def measured_traffic(launch):
     """DRAM bytes (read + write) of one advect launch from the committed ncu
-    capture, or None when the kernel source has changed since the capture or
-    the capture was of another launch shape."""
+    captures (one per launch shape), or None when the kernel source has
+    changed since the captures or none was of this launch shape."""
     rec = os.path.join(ROOT, "profiles", "advect_turb256_traffic.json")
     if not os.path.exists(rec):
         return None
@@ -315,7 +315,10 @@ def measured_traffic(launch):
     if not kernel_source_sha256().startswith(d["kernel_source_sha256_prefix"]):
         return None
     shape = [launch["threads_per_cta"], launch["particles_per_thread"], launch["reg_cap"]]
-    return d["dram_bytes_per_launch"] if d.get("launch_shape") == shape else None
+    for c in d.get("captures", []):
+        if c.get("launch_shape") == shape:
+            return c["dram_bytes_per_launch"]
+    return None
 
 
 def run_ours(args):
