@@ -81,3 +81,62 @@ def test_stitching_at_lattice_points_and_outside():
     assert np.allclose(path[1, 0], E[1 + 4 * (2 + 4 * 0)])
     assert np.all(np.isnan(path[1, 1]))                      # outside the lattice
     assert np.allclose(path[1, 2], E[3 + 4 * (3 + 4 * 3)])   # upper corner
+
+
+def _quadratic_flow_map(X, T):
+    # u = (x^2, 0, 0): x(T) = x0 / (1 - x0 T), y and z fixed
+    out = X.copy()
+    out[:, 0] = X[:, 0] / (1.0 - X[:, 0] * T)
+    return out
+
+
+def test_stitching_error_is_second_order_in_the_seed_spacing():
+    # Sec. 3.3 (Eq. global): the post hoc interpolation of a flow map from
+    # basis flows spaced h_x apart errs by O(h_x^2), bounded by the Hessian of
+    # the flow map (d^2/8 h_x^2 max|H| for one interval). The flow map of
+    # u = (x^2, 0, 0) over T is known in closed form and is not affine in x,
+    # so its basis flows are taken exact and only the interpolation errs: the
+    # mean error must fall about 4x each time h_x halves, stay under the 1D
+    # bound h_x^2 / 8 max|F''| (which implies the paper's d^2/8 form), and y
+    # and z (affine) must be reproduced to rounding.
+    T, box = 0.5, 0.5
+    F2_max = 2.0 * T / (1.0 - box * T) ** 3          # max of d^2/dx0^2 x0 / (1 - x0 T)
+    rng = np.random.default_rng(11)
+    start = rng.uniform(0.0, box, size=(4000, 3))
+    exact = _quadratic_flow_map(start, T)
+    means = []
+    for n in (8, 16, 32, 64):
+        S, hx = (n + 1,) * 3, box / n                  # dyadic spacing: exact lattice
+        jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+        X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * hx
+        path = oracle.stitch(S, (0.0, 0.0, 0.0), (hx, hx, hx), [_quadratic_flow_map(X, T)], start)
+        err = np.abs(path[1] - exact)
+        assert np.max(err[:, 1:]) < 1e-14
+        assert np.max(err[:, 0]) <= hx * hx / 8.0 * F2_max * (1.0 + 1e-9)
+        assert np.max(err[:, 0]) <= 9.0 / 8.0 * hx * hx * F2_max
+        means.append(float(np.mean(err[:, 0])))
+    ratios = [means[k] / means[k + 1] for k in range(len(means) - 1)]
+    assert all(3.6 < r < 4.4 for r in ratios), ratios
+
+
+def test_stitched_pathline_error_stays_second_order_over_intervals():
+    # Eq. (global) for n stitched intervals: the error grows with the number
+    # of intervals but keeps the h_x^2 order. Three intervals of the same
+    # closed-form map, lattice spacings 1/16 and 1/32 of the box.
+    T, box = 0.25, 0.5
+    rng = np.random.default_rng(12)
+    start = rng.uniform(0.0, 0.2, size=(2000, 3))      # stays inside for 3 intervals
+    exact = start.copy()
+    for _ in range(3):
+        exact = _quadratic_flow_map(exact, T)
+    assert np.max(exact[:, 0]) < box
+    errs = []
+    for n in (16, 32):
+        S, hx = (n + 1,) * 3, box / n
+        jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+        X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * hx
+        E = _quadratic_flow_map(X, T)
+        path = oracle.stitch(S, (0.0, 0.0, 0.0), (hx, hx, hx), [E, E, E], start)
+        assert np.all(np.isfinite(path[3]))
+        errs.append(float(np.mean(np.abs(path[3] - exact)[:, 0])))
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
