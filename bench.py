@@ -1012,17 +1012,20 @@ def large_leg(args, dev, stream):
     # new pathlines (Sec. 3.2 / 4.3 second context): stitched through the 3
     # intervals' basis flows of BTO (reconstructed) and of the global map,
     # against the RK4 ground truth advected without interval resets
+    # (trilinear over the lattice cell, and the paper's barycentric
+    # coordinates in the cell's Kuhn tetrahedron)
     paths = {}
     for name, sets in (("bto", filled_sets), ("global", global_sets)):
         table = torch.tensor([t.data_ptr() for t in sets], dtype=torch.int64, device=dev)
-        path = torch.empty((NI + 1, nq, 3), dtype=torch.float32, device=dev)
-        bto.bto_stitch_pathlines((G, G, G), (0, 0, 0), (h, h, h), NI, table, nq, starts, path)
-        paths[name] = path
+        for scheme, suffix in ((bto.BTO_STITCH_TRILINEAR, ""), (bto.BTO_STITCH_BARYCENTRIC, "_barycentric")):
+            path = torch.empty((NI + 1, nq, 3), dtype=torch.float32, device=dev)
+            bto.bto_stitch_pathlines_ex((G, G, G), (0, 0, 0), (h, h, h), NI, table, nq, starts, path, scheme)
+            paths[name + suffix] = path
     torch.cuda.synchronize()
     path_err = []
     for k in range(1, NI + 1):
         row = {"after_interval": k}
-        for name in ("bto", "global"):
+        for name in ("bto", "global", "bto_barycentric", "global_barycentric"):
             e = (paths[name][k] - truth[k]).double().norm(dim=1) / h
             fin = torch.isfinite(e)
             row[name + "_mean_l2_cells"] = e[fin].mean().item() if fin.any() else None

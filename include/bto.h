@@ -289,9 +289,9 @@ BTO_API bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_end
 
 /* Pathline stitching (Sec. 3.2): new particles follow the basis flows of
  * successive intervals. In interval k a particle's next position is the
- * trilinear interpolant (Eq. 1 per axis; the lattice stand-in for the
- * paper's barycentric interpolation) of the end positions of the 8 basis
- * flows of its seed-lattice cell. Outside the lattice, or in a cell with a
+ * trilinear interpolant (Eq. 1 per axis; bto_stitch_pathlines_ex also
+ * offers the paper's barycentric interpolation) of the end positions of the
+ * 8 basis flows of its seed-lattice cell. Outside the lattice, or in a cell with a
  * missing (NaN) basis flow, the particle stops and its later positions are
  * NaN.
  *   lattice[3], origin[3], spacing[3]  seed lattice (host): point j at
@@ -306,6 +306,33 @@ BTO_API bto_status bto_stitch_pathlines(const int32_t lattice[3], const float or
                                         const float spacing[3], int32_t intervals,
                                         const float *const *d_ends_table, int64_t nq,
                                         const float *d_start, float *d_path, bto_stream stream);
+
+/* Interpolation of the basis flows in bto_stitch_pathlines_ex. */
+typedef enum {
+    BTO_STITCH_TRILINEAR = 0,   /* the 8 corners of the lattice cell (Eq. 1 per axis) */
+    BTO_STITCH_BARYCENTRIC = 1  /* barycentric coordinates in a tetrahedron of the cell */
+} bto_stitch_scheme;
+
+/* bto_stitch_pathlines with a choice of interpolant (Sec. 3.2: the paper
+ * follows a Delaunay neighbourhood of basis flows with barycentric
+ * coordinates). On a complete seed lattice the 8 corners of a cell lie on
+ * one sphere, so any face-conforming split of the cells into tetrahedra is
+ * a Delaunay triangulation of the start points; BTO_STITCH_BARYCENTRIC
+ * takes the Kuhn split, the 6 tetrahedra around the cell's main diagonal.
+ * For fractional cell coordinates t sorted in decreasing order,
+ * t_a >= t_b >= t_c (ties keep the axis order x, y, z), the tetrahedron is
+ * corner 0, corner 0 + e_a, corner 0 + e_a + e_b, corner 0 + (1, 1, 1),
+ * with weights 1 - t_a, t_a - t_b, t_b - t_c, t_c. A particle stops (NaN)
+ * outside the lattice or when a vertex of its tetrahedron is missing; for
+ * BTO_STITCH_TRILINEAR, when any corner of its cell is missing.
+ *   scheme       a bto_stitch_scheme value; anything else is
+ *                BTO_ERR_INVALID_ARG
+ *   other arguments as in bto_stitch_pathlines */
+BTO_API bto_status bto_stitch_pathlines_ex(const int32_t lattice[3], const float origin[3],
+                                           const float spacing[3], int32_t intervals,
+                                           const float *const *d_ends_table, int64_t nq,
+                                           const float *d_start, float *d_path, int32_t scheme,
+                                           bto_stream stream);
 
 /* ---- Adjoint: gradients of a loss on end positions ----------------------
  *

@@ -315,12 +315,25 @@ def fill_lattice(S, ends: np.ndarray, valid: np.ndarray):
     return out.reshape(-1, 3), status.reshape(-1)
 
 
-def stitch(S, origin, spacing, ends_list, start):
+def stitch(S, origin, spacing, ends_list, start, scheme: str = "trilinear"):
     """Pathline stitching (Sec. 3.2) on a seed lattice: in interval k the next
-    position is the trilinear interpolant (Eq. 1 per axis) of the end
-    positions of the 8 basis flows of the particle's lattice cell. Outside
-    the lattice or next to a missing (NaN) entry the particle stops (NaN).
-    Returns (intervals + 1, nq, 3)."""
+    position interpolates the end positions of the basis flows around the
+    particle's lattice cell. ``scheme``:
+
+    * ``"trilinear"``: Eq. 1 per axis over the cell's 8 corners;
+    * ``"barycentric"``: the paper's barycentric coordinates in a Delaunay
+      tetrahedron of the start points. The 8 corners of a lattice cell lie on
+      one sphere, so every face-conforming split of the cells is a Delaunay
+      triangulation; this is the Kuhn split (6 tetrahedra sharing the main
+      diagonal). With the fractional coordinates sorted t_a >= t_b >= t_c
+      (ties kept in axis order), the particle's tetrahedron has vertices
+      0, e_a, e_a + e_b, (1, 1, 1) and its barycentric weights are
+      1 - t_a, t_a - t_b, t_b - t_c, t_c.
+
+    Outside the lattice, or when an entry the interpolant uses is missing
+    (NaN), the particle stops (NaN). Returns (intervals + 1, nq, 3)."""
+    if scheme not in ("trilinear", "barycentric"):
+        raise ValueError(scheme)
     S = [int(v) for v in S]
     o = np.asarray(origin, dtype=np.float32).astype(np.float64)
     sp = np.asarray(spacing, dtype=np.float32).astype(np.float64)
@@ -336,12 +349,22 @@ def stitch(S, origin, spacing, ends_list, start):
             cell = [min(int(np.floor(u[a])), max(S[a] - 2, 0)) for a in range(3)]
             t = [u[a] - cell[a] for a in range(3)]
             acc = np.zeros(3)
-            for c in range(2):
-                for b in range(2):
-                    for a in range(2):
-                        w = (t[0] if a else 1 - t[0]) * (t[1] if b else 1 - t[1]) * (t[2] if c else 1 - t[2])
-                        j = [min(cell[0] + a, S[0] - 1), min(cell[1] + b, S[1] - 1), min(cell[2] + c, S[2] - 1)]
-                        acc += w * E[j[2], j[1], j[0]]
+            if scheme == "trilinear":
+                for c in range(2):
+                    for b in range(2):
+                        for a in range(2):
+                            w = (t[0] if a else 1 - t[0]) * (t[1] if b else 1 - t[1]) * (t[2] if c else 1 - t[2])
+                            j = [min(cell[0] + a, S[0] - 1), min(cell[1] + b, S[1] - 1), min(cell[2] + c, S[2] - 1)]
+                            acc += w * E[j[2], j[1], j[0]]
+            else:
+                axes = sorted(range(3), key=lambda a: -t[a])        # stable: ties keep x, y, z
+                ts = [t[a] for a in axes]
+                weights = [1 - ts[0], ts[0] - ts[1], ts[1] - ts[2], ts[2]]
+                j = list(cell)
+                for m in range(4):
+                    if m > 0:
+                        j[axes[m - 1]] = min(j[axes[m - 1]] + 1, S[axes[m - 1]] - 1)
+                    acc += weights[m] * E[j[2], j[1], j[0]]
             nxt[i] = acc
         x = nxt
         path.append(x.copy())

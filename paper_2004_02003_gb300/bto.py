@@ -28,6 +28,8 @@ BTO_ERR_TIMEOUT = 5
 BTO_ERR_UNSUPPORTED = 6
 BTO_FIELD_F3_AOS = 0
 BTO_FIELD_F4_AOS = 1
+BTO_STITCH_TRILINEAR = 0
+BTO_STITCH_BARYCENTRIC = 1
 
 _lib = None
 
@@ -72,6 +74,8 @@ def _declare(lib):
         "bto_fill_lattice": ([c_i32p, vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_stitch_pathlines": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp],
                                  ctypes.c_int),
+        "bto_stitch_pathlines_ex": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp,
+                                     ctypes.c_int32, vp], ctypes.c_int),
         "bto_tape_create": ([c_i32p, c_fp, c_fp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                              ctypes.POINTER(vp)], ctypes.c_int),
         "bto_tape_num_particles": ([vp], ctypes.c_int64),
@@ -285,6 +289,14 @@ def bto_stitch_pathlines(lattice, origin, spacing, intervals: int, d_ends_table,
     _check(load().bto_stitch_pathlines(_arr(ctypes.c_int32, lattice), _arr(ctypes.c_float, origin),
                                        _arr(ctypes.c_float, spacing), int(intervals), _addr(d_ends_table), int(nq),
                                        _addr(d_start), _addr(d_path), _stream(stream)), "bto_stitch_pathlines")
+
+
+def bto_stitch_pathlines_ex(lattice, origin, spacing, intervals: int, d_ends_table, nq: int, d_start, d_path,
+                            scheme: int, stream=None) -> None:
+    _check(load().bto_stitch_pathlines_ex(_arr(ctypes.c_int32, lattice), _arr(ctypes.c_float, origin),
+                                          _arr(ctypes.c_float, spacing), int(intervals), _addr(d_ends_table),
+                                          int(nq), _addr(d_start), _addr(d_path), int(scheme), _stream(stream)),
+           "bto_stitch_pathlines_ex")
 
 
 def bto_tape_create(extent_cells, origin, spacing, num_particles: int, cycles: int,

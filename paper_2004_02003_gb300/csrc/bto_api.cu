@@ -1037,6 +1037,14 @@ bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_ends, const
 bto_status bto_stitch_pathlines(const int32_t lattice[3], const float origin[3], const float spacing[3],
                                 int32_t intervals, const float *const *d_ends_table, int64_t nq,
                                 const float *d_start, float *d_path, bto_stream stream) {
+    return bto_stitch_pathlines_ex(lattice, origin, spacing, intervals, d_ends_table, nq, d_start, d_path,
+                                   BTO_STITCH_TRILINEAR, stream);
+}
+
+bto_status bto_stitch_pathlines_ex(const int32_t lattice[3], const float origin[3], const float spacing[3],
+                                   int32_t intervals, const float *const *d_ends_table, int64_t nq,
+                                   const float *d_start, float *d_path, int32_t scheme, bto_stream stream) {
+    if (scheme != BTO_STITCH_TRILINEAR && scheme != BTO_STITCH_BARYCENTRIC) return BTO_ERR_INVALID_ARG;
     if (!lattice || !origin || !spacing || !d_ends_table || !d_start || !d_path) return BTO_ERR_INVALID_ARG;
     if (intervals < 1 || nq < 1) return BTO_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
@@ -1049,7 +1057,7 @@ bto_status bto_stitch_pathlines(const int32_t lattice[3], const float origin[3],
     BTO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nq + 255) / 256, (int64_t)sms * 8));
     BTO_CUDA(bto::launch_stitch(lattice, origin, spacing, intervals, d_ends_table, nq, d_start, d_path, grid,
-                                (cudaStream_t)stream));
+                                (cudaStream_t)stream, scheme == BTO_STITCH_BARYCENTRIC));
     return BTO_OK;
 }
 

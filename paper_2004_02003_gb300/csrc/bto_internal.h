@@ -162,7 +162,7 @@ cudaError_t launch_ingest(const void *field, const void *const *fields, int b, i
                           int grid, cudaStream_t s);
 cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
                           const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,
-                          cudaStream_t s);
+                          cudaStream_t s, bool barycentric);
 cudaError_t launch_fill_lattice(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
                                 uint8_t *status, int grid, cudaStream_t s);
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,

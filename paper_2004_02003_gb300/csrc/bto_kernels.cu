@@ -310,10 +310,19 @@ __global__ void fill_lattice_kernel(int3 S, const float *__restrict__ ends, cons
 
 // Pathline stitching (Sec. 3.2): a new particle follows the basis flows of
 // successive intervals. At the start of interval k it sits in a cell of the
-// seed lattice; its position at the end of the interval is the trilinear
-// interpolant (Eq. 1 per axis) of the end positions of that cell's 8 basis
-// flows. A particle outside the lattice, or whose cell has a missing basis
-// flow (NaN), stops: its later positions are NaN.
+// seed lattice; its position at the end of the interval interpolates the end
+// positions of that cell's basis flows:
+//   trilinear    the 8 corners, Eq. 1 per axis;
+//   barycentric  the 4 vertices of the cell's Kuhn tetrahedron holding it
+//                (the paper's barycentric coordinates over a Delaunay
+//                neighbourhood; the cells of a full lattice are cospherical,
+//                so the Kuhn split is a Delaunay triangulation): with the
+//                fractional coordinates sorted t_a >= t_b >= t_c (a stable
+//                sort, ties in axis order), vertices 0, e_a, e_a + e_b,
+//                (1, 1, 1) and weights 1 - t_a, t_a - t_b, t_b - t_c, t_c.
+// A particle outside the lattice, or next to a missing basis flow (NaN) that
+// its interpolant uses, stops: its later positions are NaN.
+template <bool BARY>
 __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t intervals,
                               const float *const *__restrict__ ends_table, int64_t nq,
                               const float *__restrict__ start, float *__restrict__ path) {
@@ -333,18 +342,39 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
                 const float fx = u - ix, fy = v - iy, fz = w - iz;
                 const float *E = ends_table[k];
                 float acc[3] = {0.f, 0.f, 0.f};
+                if (BARY) {
+                    // stable descending sort of (fx, fy, fz) with the axes
+                    int ax[3] = {0, 1, 2};
+                    float t[3] = {fx, fy, fz};
+                    if (t[1] > t[0]) { float q = t[0]; t[0] = t[1]; t[1] = q; int r = ax[0]; ax[0] = ax[1]; ax[1] = r; }
+                    if (t[2] > t[1]) {
+                        float q = t[1]; t[1] = t[2]; t[2] = q; int r = ax[1]; ax[1] = ax[2]; ax[2] = r;
+                        if (t[1] > t[0]) { q = t[0]; t[0] = t[1]; t[1] = q; r = ax[0]; ax[0] = ax[1]; ax[1] = r; }
+                    }
+                    int j[3] = {ix, iy, iz};
+                    const int ext[3] = {S.x, S.y, S.z};
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
+                    for (int m = 0; m < 4; ++m) {
+                        if (m > 0) j[ax[m - 1]] = min(j[ax[m - 1]] + 1, ext[ax[m - 1]] - 1);
+                        const float wgt = m == 0 ? 1.f - t[0] : (m == 3 ? t[2] : t[m - 1] - t[m]);
+                        const int64_t p = j[0] + (int64_t)S.x * (j[1] + (int64_t)S.y * j[2]);
 #pragma unroll
-                    for (int b = 0; b < 2; ++b)
+                        for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
+                    }
+                } else {
 #pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const int jx = min(ix + a, S.x - 1), jy = min(iy + b, S.y - 1), jz = min(iz + c, S.z - 1);
-                            const float wgt = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (c ? fz : 1.f - fz);
-                            const int64_t p = jx + (int64_t)S.x * (jy + (int64_t)S.y * jz);
+                    for (int c = 0; c < 2; ++c)
 #pragma unroll
-                            for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
-                        }
+                        for (int b = 0; b < 2; ++b)
+#pragma unroll
+                            for (int a = 0; a < 2; ++a) {
+                                const int jx = min(ix + a, S.x - 1), jy = min(iy + b, S.y - 1), jz = min(iz + c, S.z - 1);
+                                const float wgt = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (c ? fz : 1.f - fz);
+                                const int64_t p = jx + (int64_t)S.x * (jy + (int64_t)S.y * jz);
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
+                            }
+                }
                 nx = acc[0]; ny = acc[1]; nz = acc[2];
             }
             x = nx; y = ny; z = nz;
@@ -442,10 +472,14 @@ cudaError_t launch_ingest(const void *field, const void *const *fields, int b, i
 
 cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
                           const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,
-                          cudaStream_t s) {
-    stitch_kernel<<<grid, 256, 0, s>>>(make_int3(S[0], S[1], S[2]), make_float3(origin[0], origin[1], origin[2]),
-                                       make_float3(1.f / spacing[0], 1.f / spacing[1], 1.f / spacing[2]),
-                                       intervals, ends_table, nq, start, path);
+                          cudaStream_t s, bool barycentric) {
+    const int3 S3 = make_int3(S[0], S[1], S[2]);
+    const float3 o = make_float3(origin[0], origin[1], origin[2]);
+    const float3 inv = make_float3(1.f / spacing[0], 1.f / spacing[1], 1.f / spacing[2]);
+    if (barycentric)
+        stitch_kernel<true><<<grid, 256, 0, s>>>(S3, o, inv, intervals, ends_table, nq, start, path);
+    else
+        stitch_kernel<false><<<grid, 256, 0, s>>>(S3, o, inv, intervals, ends_table, nq, start, path);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,19 @@ def test_null_context_calls(lib):
     lib.bto_tape_destroy(None)
 
 
+def test_stitch_argument_checks(lib):
+    lat = (ctypes.c_int32 * 3)(4, 4, 4)
+    org = (ctypes.c_float * 3)(0, 0, 0)
+    spc = (ctypes.c_float * 3)(1, 1, 1)
+    fake = ctypes.c_void_p(4096)        # never dereferenced: the checks fail first
+    for scheme in (-1, 2, 7):
+        assert lib.bto_stitch_pathlines_ex(lat, org, spc, 1, fake, 1, fake, fake, scheme,
+                                           None) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_stitch_pathlines_ex(lat, org, spc, 0, fake, 1, fake, fake, bto.BTO_STITCH_BARYCENTRIC,
+                                       None) == bto.BTO_ERR_INVALID_ARG
+    assert lib.bto_stitch_pathlines(None, org, spc, 1, fake, 1, fake, fake, None) == bto.BTO_ERR_INVALID_ARG
+
+
 def test_batch_argument_checks(lib):
     out = ctypes.c_void_p()
     ext = (ctypes.c_int32 * 6)(4, 4, 4, 4, -1, 4)

@@ -558,6 +558,48 @@ def test_stitching_matches_oracle():
     assert np.max(np.abs(g[ok] - ref[ok])) < 1e-5
 
 
+def test_barycentric_stitching_matches_oracle():
+    # The Kuhn-tetrahedron barycentric interpolant on the GPU against the
+    # oracle, with missing entries (a particle stops only when a vertex of
+    # its own tetrahedron is missing) and starts on lattice points and on
+    # the tie planes fx = fy = fz.
+    import torch
+    rng = np.random.default_rng(23)
+    S, o, sp = (17, 13, 11), (0.2, -0.1, 0.3), (0.125, 0.25, 0.125)
+    P = S[0] * S[1] * S[2]
+    jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+    X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * np.asarray(sp) + np.asarray(o)
+    ends = []
+    for k in range(3):          # bilinear terms: the two interpolants differ
+        E = X + 0.05 * np.sin(3 * X[:, [1, 2, 0]] + k) + 0.3 * X * X[:, [1, 2, 0]] + 0.02 * k
+        E[rng.random(P) < 0.01] = np.nan
+        ends.append(E.astype(np.float32))
+    n_rand = 600
+    u = rng.random((n_rand, 3)) * (np.asarray(S) - 1)
+    u[:50] = np.floor(u[:50])                               # lattice points
+    u[50:100, 1] = np.floor(u[50:100, 1]) + (u[50:100, 0] - np.floor(u[50:100, 0]))   # fx = fy
+    u[100:150, 2] = np.floor(u[100:150, 2]) + (u[100:150, 0] - np.floor(u[100:150, 0]))  # fx = fz
+    start = (np.asarray(o) + u * np.asarray(sp)).astype(np.float32)
+    ref = oracle.stitch(S, o, sp, [e.astype(np.float64) for e in ends], start.astype(np.float64),
+                        scheme="barycentric")
+    tri = oracle.stitch(S, o, sp, [e.astype(np.float64) for e in ends], start.astype(np.float64))
+    dev_e = [torch.from_numpy(e).cuda() for e in ends]
+    table = torch.tensor([t.data_ptr() for t in dev_e], dtype=torch.int64, device="cuda")
+    path = torch.empty((4, n_rand, 3), dtype=torch.float32, device="cuda")
+    bto.bto_stitch_pathlines_ex(S, o, sp, 3, table, n_rand, torch.from_numpy(start).cuda(), path,
+                                bto.BTO_STITCH_BARYCENTRIC)
+    torch.cuda.synchronize()
+    g = path.cpu().numpy()
+    assert np.array_equal(np.isnan(g), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.isnan(ref).any() and ok.any()
+    assert np.max(np.abs(g[ok] - ref[ok])) < 1e-5
+    # the two interpolants differ (and barycentric keeps more pathlines)
+    both = ok & ~np.isnan(tri)
+    assert np.max(np.abs(ref[both] - tri[both])) > 1e-4
+    assert ok.sum() > (~np.isnan(tri)).sum()
+
+
 def test_batched_f4_graph_and_exits_equal_f3_per_cycle():
     # The batched form with F4 fields through the interval graph, with exit
     # locations, equals the batched F3 form driven cycle by cycle.

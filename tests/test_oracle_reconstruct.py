@@ -140,3 +140,83 @@ def test_stitched_pathline_error_stays_second_order_over_intervals():
         assert np.all(np.isfinite(path[3]))
         errs.append(float(np.mean(np.abs(path[3] - exact)[:, 0])))
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+def _unit_cell_lattice(E8):
+    # corner (a, b, c) of the unit cell -> lattice entry, x fastest
+    return np.asarray(E8, dtype=np.float64).reshape(8, 3)
+
+
+def test_barycentric_stitching_worked_example():
+    # Kuhn split of the unit cell (Sec. 3.2's barycentric coordinates over a
+    # Delaunay tetrahedron). At (0.7, 0.2, 0.4): x > z > y, so the
+    # tetrahedron is (0,0,0), (1,0,0), (1,0,1), (1,1,1) with weights
+    # 1 - 0.7, 0.7 - 0.4, 0.4 - 0.2, 0.2. At the cell centre every fraction
+    # is 1/2: the weights are 1/2 on (0,0,0) and on (1,1,1), nothing else.
+    rng = np.random.default_rng(13)
+    E = rng.standard_normal((8, 3))          # index a + 2b + 4c
+    c000, c100, c101, c111 = E[0], E[1], E[1 + 4], E[7]
+    path = oracle.stitch((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), [E],
+                         np.array([[0.7, 0.2, 0.4], [0.5, 0.5, 0.5]]), scheme="barycentric")
+    assert np.allclose(path[1, 0], 0.3 * c000 + 0.3 * c100 + 0.2 * c101 + 0.2 * c111, atol=1e-14)
+    assert np.allclose(path[1, 1], 0.5 * c000 + 0.5 * c111, atol=1e-14)
+    # bilinear data x*y: trilinear is exact at the centre (1/4), the Kuhn
+    # tetrahedron gives the diagonal average (1/2)
+    xy = np.array([[float(a * b)] * 3 for c in range(2) for b in range(2) for a in range(2)])
+    centre = np.array([[0.5, 0.5, 0.5]])
+    tri = oracle.stitch((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), [xy], centre)
+    bary = oracle.stitch((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), [xy], centre, scheme="barycentric")
+    assert np.allclose(tri[1, 0], 0.25) and np.allclose(bary[1, 0], 0.5)
+
+
+def test_barycentric_stitching_composes_affine_maps_and_is_continuous():
+    S, o, sp = (12, 10, 9), (0.0, 0.0, 0.0), (0.5, 0.5, 0.5)
+    M1 = np.array([[1.0, 0.05, 0.0], [-0.05, 1.0, 0.02], [0.0, 0.01, 0.98]])
+    M2 = np.array([[0.97, 0.0, 0.03], [0.02, 1.01, 0.0], [0.0, -0.02, 1.0]])
+    b1, b2 = np.array([0.1, -0.05, 0.2]), np.array([-0.1, 0.1, 0.05])
+    E1, E2 = _affine_lattice(S, o, sp, M1, b1), _affine_lattice(S, o, sp, M2, b2)
+    rng = np.random.default_rng(14)
+    start = rng.uniform(1.5, 3.5, size=(50, 3))
+    path = oracle.stitch(S, o, sp, [E1, E2], start, scheme="barycentric")
+    want1 = start @ M1.T + b1
+    assert np.max(np.abs(path[1] - want1)) < 1e-12
+    assert np.max(np.abs(path[2] - (want1 @ M2.T + b2))) < 1e-12
+    # across the faces between tetrahedra (fx = fy, fy = fz) and between
+    # cells the interpolant is continuous: points eps apart differ by O(eps)
+    E = rng.standard_normal((S[0] * S[1] * S[2], 3))
+    eps = 1e-9
+    base = np.array([[1.3, 1.3, 2.2], [1.8, 2.1, 2.1], [2.0, 1.7, 1.1], [1.6, 1.6, 1.6]])
+    for d in (np.array([eps, -eps, 0.0]), np.array([0.0, eps, -eps]), np.array([eps, 0.0, 0.0])):
+        p_lo = oracle.stitch(S, o, sp, [E], base - d, scheme="barycentric")[1]
+        p_hi = oracle.stitch(S, o, sp, [E], base + d, scheme="barycentric")[1]
+        assert np.max(np.abs(p_hi - p_lo)) < 1e-6
+
+
+def test_barycentric_stitching_is_second_order_and_uses_only_its_tetrahedron():
+    T, box = 0.5, 0.5
+    rng = np.random.default_rng(15)
+    start = rng.uniform(0.0, box, size=(4000, 3))
+    exact = _quadratic_flow_map(start, T)
+    means = []
+    for n in (8, 16, 32):
+        S, hx = (n + 1,) * 3, box / n
+        jz, jy, jx = np.meshgrid(np.arange(S[2]), np.arange(S[1]), np.arange(S[0]), indexing="ij")
+        X = np.stack([jx, jy, jz], axis=-1).reshape(-1, 3) * hx
+        path = oracle.stitch(S, (0.0, 0.0, 0.0), (hx, hx, hx), [_quadratic_flow_map(X, T)], start,
+                             scheme="barycentric")
+        err = np.abs(path[1] - exact)
+        assert np.max(err[:, 1:]) < 1e-14
+        means.append(float(np.mean(err[:, 0])))
+    ratios = [means[k] / means[k + 1] for k in range(len(means) - 1)]
+    assert all(3.6 < r < 4.4 for r in ratios), ratios
+    # a missing entry off the particle's tetrahedron does not stop it; one
+    # on it does (trilinear stops for either)
+    E = rng.standard_normal((8, 3))
+    q = np.array([[0.7, 0.2, 0.4]])                      # tetrahedron 000, 100, 101, 111
+    off, on = E.copy(), E.copy()
+    off[2] = np.nan                                      # corner (0, 1, 0)
+    on[5] = np.nan                                       # corner (1, 0, 1)
+    grid = ((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    assert np.all(np.isfinite(oracle.stitch(*grid, [off], q, scheme="barycentric")[1]))
+    assert np.all(np.isnan(oracle.stitch(*grid, [on], q, scheme="barycentric")[1]))
+    assert np.all(np.isnan(oracle.stitch(*grid, [off], q)[1]))
