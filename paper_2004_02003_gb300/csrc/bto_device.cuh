@@ -20,7 +20,9 @@ __device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(
 
 struct Cell {
     int ix, iy, iz;
-    float v[8][3];  // corner (a, b, c) -> index a + 2b + 4c
+    // corner (a, b, c) -> index a + 2b + 4c; each x-edge's second entry
+    // holds the difference v(a = 1) - v(a = 0), formed once per load
+    float v[8][3];
 };
 
 // The 8 corner nodes of cell (ix, iy, iz), as four x-neighbour pairs. F4
@@ -50,6 +52,23 @@ __device__ __forceinline__ void load_cell(const void *__restrict__ field, uint32
             }
         }
     }
+}
+
+// Trilinear interpolation from a cell whose x-edges hold (value, difference):
+// fma(fx, d, a) equals lerp1(a, b, fx) with d = b - a formed at load time.
+__device__ __forceinline__ float3 trilerp_dx(const float (&v)[8][3], float fx, float fy, float fz) {
+    float r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float c00 = fmaf(fx, v[1][k], v[0][k]);
+        const float c10 = fmaf(fx, v[3][k], v[2][k]);
+        const float c01 = fmaf(fx, v[5][k], v[4][k]);
+        const float c11 = fmaf(fx, v[7][k], v[6][k]);
+        const float c0 = lerp1(c00, c10, fy);
+        const float c1 = lerp1(c01, c11, fy);
+        r[k] = lerp1(c0, c1, fz);
+    }
+    return make_float3(r[0], r[1], r[2]);
 }
 
 __device__ __forceinline__ float3 trilerp(const float (&v)[8][3], float fx, float fy, float fz) {
@@ -108,9 +127,13 @@ __device__ __forceinline__ float3 sample(Cell &C, const Src &src, const Geo &g, 
     const int iz = min(max(__float2int_rd(z), 0), g.nz - 1);
     if (ix != C.ix || iy != C.iy || iz != C.iz) {
         src.load(ix, iy, iz, C.v);
+#pragma unroll
+        for (int e = 0; e < 8; e += 2)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) C.v[e + 1][k] -= C.v[e][k];
         C.ix = ix; C.iy = iy; C.iz = iz;
     }
-    return trilerp(C.v, x - (float)ix, y - (float)iy, z - (float)iz);
+    return trilerp_dx(C.v, x - (float)ix, y - (float)iy, z - (float)iz);
 }
 
 // One RK4 step in cell units (s = dt / h per axis). Returns 0 and moves x
