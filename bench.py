@@ -62,7 +62,7 @@ def parse():
                     help="field layout handed to the library (f4 pads each node to 16 bytes)")
     ap.add_argument("--ingest", action="store_true", help="repack F3 fields to 16-byte nodes per block (H1)")
     ap.add_argument("--launch", default="", help="threads,ppt,ctas_per_sm,reg_cap (default: library's)")
-    ap.add_argument("--e2e-streams", type=int, default=4, help="copy streams of the end-to-end leg")
+    ap.add_argument("--e2e-streams", type=int, default=1, help="copy streams of the end-to-end leg")
     ap.add_argument("--only", default="", choices=["", "batched"],
                     help="run one workload leg alone and print its JSON (for profiling)")
     ap.add_argument("--no-plain", action="store_true", help="batched leg: skip the 512-context plain comparison")
@@ -1050,27 +1050,33 @@ def e2e(args, ctx, fields, dt, dev, stream, nb, world=1):
     import torch
     L = INTERVAL
     R = 8  # pinned host ring of per-cycle fields (cycle c uses host[c % R])
-    host = [[torch.empty(f.shape, dtype=torch.float32, pin_memory=True) for f in fields[0]] for _ in range(R)]
+    # each cycle's block fields lie side by side, on the host and in the two
+    # device slots, so that a copy stream moves its share in one copy
+    shape = tuple(fields[0][0].shape)
+    host = [torch.empty((nb,) + shape, dtype=torch.float32, pin_memory=True) for _ in range(R)]
     for r in range(R):
         for b in range(nb):
             host[r][b].copy_(fields[r][b])
-    slots = [[torch.empty_like(f) for f in fields[0]] for _ in range(2)]
-    slot_ptrs = [torch.tensor([t.data_ptr() for t in s], dtype=torch.int64, device=dev) for s in slots]
+    slots = [torch.empty((nb,) + shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    slot_ptrs = [torch.tensor([slot[b].data_ptr() for b in range(nb)], dtype=torch.int64, device=dev)
+                 for slot in slots]
     def host_out():
         return {"seeds": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
                 "ends": torch.empty((ctx.P, 3), dtype=torch.float32, pin_memory=True),
                 "valid": torch.empty((ctx.P,), dtype=torch.uint8, pin_memory=True),
                 "exit_cycle": torch.empty((ctx.P,), dtype=torch.int32, pin_memory=True)}
     out_host = [host_out(), host_out()]      # interval k's results land in out_host[k % 2]
-    # each cycle's block fields are split over K copy streams (each stream's
-    # copies run on a copy engine of its own when one is free)
+    # each cycle's block fields are split over K copy streams, one copy of
+    # contiguous blocks each (concurrent copies contend for the host link:
+    # one stream measured fastest)
     K = max(1, min(args.e2e_streams, nb))
+    chunks = [(j * nb // K, (j + 1) * nb // K) for j in range(K)]
     copy_streams = [torch.cuda.Stream(device=dev) for _ in range(K)]
     out_dev = ctx.alloc_outputs(dev)
     copied = [[torch.cuda.Event() for _ in range(K)] for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
     landed = [torch.cuda.Event() for _ in range(2)]
-    h2d_bytes = sum(t.numel() * 4 for t in host[0])
+    h2d_bytes = host[0].numel() * 4
     d2h_bytes = sum(t.numel() * t.element_size() for t in out_host[0].values())
     gc = [0]                                   # cycles enqueued so far (slot parity)
 
@@ -1084,8 +1090,8 @@ def e2e(args, ctx, fields, dt, dev, stream, nb, world=1):
                 with torch.cuda.stream(cs):
                     if gc[0] >= 2:
                         cs.wait_event(consumed[s])
-                    for b in range(j, nb, K):
-                        slots[s][b].copy_(host[c % R][b], non_blocking=True)
+                    b0, b1 = chunks[j]
+                    slots[s][b0:b1].copy_(host[c % R][b0:b1], non_blocking=True)
                     copied[s][j].record(cs)
             for j in range(K):
                 stream.wait_event(copied[s][j])
