@@ -67,6 +67,9 @@ def parse():
                     help="run one workload leg alone and print its JSON (for profiling)")
     ap.add_argument("--no-plain", action="store_true", help="batched leg: skip the 512-context plain comparison")
     ap.add_argument("--tile", default="", help="tx,ty,tz[,threads]: tiled advection kernel (default: off)")
+    ap.add_argument("--stride", type=int, default=STRIDE,
+                    help="seed stride of the main leg, to profile it at other densities "
+                         "(other than 2 it skips the other legs)")
     ap.add_argument("--fields", type=int, default=INTERVAL,
                     help="distinct per-cycle fields kept in HBM (cycle c uses field c %% N); "
                          "fewer fields make a small case for profiling")
@@ -336,6 +339,9 @@ def run_ours(args):
     bto.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    if args.stride != STRIDE:          # a profiling variant of the main leg only
+        args.no_extras = args.no_large = True
+        args.cpu_seconds = 0.0
 
     modes = inputs.fourier_modes(SEED, m=NMODES, kmin=1.0, kmax=16.0, drift_max=0.05)
     h = 1.0 / GLOBAL_CELLS
@@ -352,7 +358,7 @@ def run_ours(args):
     table = torch.tensor([f.data_ptr() for row in fields for f in row], dtype=torch.int64, device=dev)
     field_bytes_cycle = sum(f.numel() * 4 for f in fields[0])
 
-    ctx = bto.Context.batch(ext, org, spc, [STRIDE] * nb, L)
+    ctx = bto.Context.batch(ext, org, spc, [args.stride] * nb, L)
     layout = bto.BTO_FIELD_F4_AOS if args.layout == "f4" else bto.BTO_FIELD_F3_AOS
     ctx.set_layout(layout)
     if args.ingest:
@@ -460,7 +466,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {
             "workload": "turb256: 256^3 cells as 2x2x2 blocks of 128^3, Fourier turbulence (64 modes), "
-                        "stride 2 (2,097,152 particles), interval 100, dt=0.25 cell/max|u|",
+                        f"stride {args.stride} ({P:,} particles), interval 100, dt=0.25 cell/max|u|",
             "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
             "field_layout": args.layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
             "ingest": bool(args.ingest),
