@@ -134,7 +134,15 @@ BTO_API bto_status bto_batch_offsets(const bto_ctx *ctx, int64_t *offsets);
  * leaves the block are terminated and removed from the active set.
  *   d_field  device pointer to the block's nodes in the selected layout
  * BTO_ERR_STATE if interval_cycles cycles were already advanced since the
- * last bto_end_interval, or if ctx holds more than one block. */
+ * last bto_end_interval, or if ctx holds more than one block.
+ * The cycle's kernel (here and in bto_batch_advect_cycle) is launched with
+ * programmatic stream serialisation: its launch may overlap the tail of the
+ * kernel before it on the stream, and it reads nothing before that kernel
+ * has completed. It lets the next kernel launch early in turn: a kernel the
+ * caller launches next on the stream with programmatic serialisation must
+ * wait on its grid dependency (griddepcontrol.wait) before it reads the
+ * context's state or the caller's field; ordinary launches, copies and
+ * events wait for completion as usual. */
 BTO_API bto_status bto_advect_cycle(bto_ctx *ctx, const void *d_field, float dt,
                             bto_stream stream);
 
