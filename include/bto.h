@@ -140,9 +140,10 @@ BTO_API bto_status bto_batch_offsets(const bto_ctx *ctx, int64_t *offsets);
  * kernel before it on the stream, and it reads nothing before that kernel
  * has completed. It lets the next kernel launch early in turn: a kernel the
  * caller launches next on the stream with programmatic serialisation must
- * wait on its grid dependency (griddepcontrol.wait) before it reads the
- * context's state or the caller's field; ordinary launches, copies and
- * events wait for completion as usual. */
+ * wait on its grid dependency (griddepcontrol.wait) before it touches memory
+ * the cycle reads or writes (the context's outputs, or d_field, for
+ * instance when it writes the next cycle's field in place); ordinary
+ * launches, copies and events wait for completion as usual. */
 BTO_API bto_status bto_advect_cycle(bto_ctx *ctx, const void *d_field, float dt,
                             bto_stream stream);
 
