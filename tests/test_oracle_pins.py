@@ -343,3 +343,74 @@ def test_exit_location_for_each_stage_by_hand():
         assert st.exit_pos[0, 0] == pytest.approx(face, abs=1e-12)
         assert tuple(st.exit_pos[0, 1:]) == (4.0, 4.0)
         assert st.exit_time[0] == pytest.approx(7 + t * f, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# BTO against the global flow map, and Eq. (hx) across block faces
+# ----------------------------------------------------------------------------
+def _decomposed_abc(L, dt):
+    G, n, s = 32, 16, 2
+    h = (1.0 / G,) * 3
+    glob = [inputs.abc_field((G, G, G), (0, 0, 0), h, c * dt) for c in range(L)]
+    gg = oracle.Grid.make((G, G, G), (0.0, 0.0, 0.0), h)
+    gst = oracle.run_interval(gg, s, L, dt, lambda c: glob[c])
+    blocks = []
+    for bz in range(2):
+        for by in range(2):
+            for bx in range(2):
+                o = (bx * n * h[0], by * n * h[1], bz * n * h[2])
+                g = oracle.Grid.make((n, n, n), o, h)
+                sl = [np.ascontiguousarray(f[bz * n:bz * n + n + 1, by * n:by * n + n + 1, bx * n:bx * n + n + 1])
+                      for f in glob]
+                blocks.append(((bx, by, bz), oracle.run_interval(g, s, L, dt, lambda c, sl=sl: sl[c])))
+    vmax = max(inputs.max_speed(f) for f in glob)
+    return G, n, s, h, gst, blocks, L * dt * vmax
+
+
+def test_bto_valid_ends_equal_global_flow_map():
+    # Sec. 3.1 / Sec. 5: a particle that never leaves its block sees the
+    # same cells and node values as in the undecomposed domain (blocks share
+    # their face nodes), so its basis flow is the global flow map's, up to
+    # rounding; and it cannot have left the domain either.
+    G, n, s, h, gst, blocks, reach = _decomposed_abc(20, 0.002)
+    S, GS = n // s, G // s
+    checked = 0
+    for (bx, by, bz), st in blocks:
+        j = np.arange(S ** 3)
+        jx, jy, jz = j % S, (j // S) % S, j // (S * S)
+        gid = (jx + bx * S) + GS * ((jy + by * S) + GS * (jz + bz * S))
+        assert np.allclose(st.seeds, gst.seeds[gid], atol=1e-15)
+        v = st.valid == 1
+        assert np.all(gst.valid[gid][v] == 1)
+        assert np.max(np.abs(st.x[v] - gst.x[gid][v])) < 1e-12
+        checked += int(v.sum())
+    assert checked > 0.5 * GS ** 3
+    # BTO terminates more than the global map: particles that cross inner faces
+    assert sum(int((st.valid == 0).sum()) for _, st in blocks) > int((gst.valid == 0).sum())
+
+
+def test_eq_hx_gap_bound_across_block_faces():
+    # Eq. (hx): missing basis flows lie within the largest displacement of a
+    # face, so along the normal of a face two valid flows around a run of
+    # missing ones are at most 2 h_x + 2 reach apart. Lines along one axis
+    # whose other coordinates are farther than the reach from every face
+    # normal to them can only lose flows near faces normal to the line.
+    G, n, s, h, gst, blocks, reach = _decomposed_abc(20, 0.002)
+    S, GS = n // s, G // s
+    hx = s * h[0]
+    lat = np.zeros((GS, GS, GS), dtype=np.uint8)        # (z, y, x)
+    for (bx, by, bz), st in blocks:
+        lat[bz * S:(bz + 1) * S, by * S:(by + 1) * S, bx * S:(bx + 1) * S] = st.valid.reshape(S, S, S)
+    j = np.arange(GS) % S
+    far = np.minimum(j, S - j) * hx > reach + 1e-12
+    cross = far[:, None] & far[None, :]
+    bound = 2.0 + 2.0 * reach / hx
+    widest = 0
+    for axis in range(3):
+        lines = np.moveaxis(lat, axis, -1)[cross]
+        assert lines.shape[0] > 0
+        for line in lines[np.any(lines == 0, axis=1)]:
+            ok = np.flatnonzero(line == 1)
+            if ok.size >= 2:
+                widest = max(widest, int(np.diff(ok).max()))
+    assert 1 < widest <= bound, (widest, bound)
