@@ -391,7 +391,7 @@ bto_status bto_tape_create(const int32_t extent_cells[3], const float origin[3],
     int64_t nodes = 1;
     for (int a = 0; a < 3; ++a) {
         const int32_t n = extent_cells[a];
-        if (n < 1 || n > (1 << 24) || !std::isfinite(origin[a]) || !std::isfinite(spacing[a]) || !(spacing[a] > 0.f))
+        if (n < 1 || n > (1 << 23) || !std::isfinite(origin[a]) || !std::isfinite(spacing[a]) || !(spacing[a] > 0.f))
             return BTO_ERR_INVALID_ARG;
         B.n[a] = n;
         B.nn[a] = n + 1;

@@ -434,7 +434,7 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
             const float o = origins[3 * b + a], h = spacings[3 * b + a];
             if (n < 1 || !std::isfinite(o) || !finite_pos(h)) return BTO_ERR_INVALID_ARG;
             // cell coordinates must stay exact integers at every node
-            if (n > (1 << 24)) return BTO_ERR_INVALID_ARG;
+            if (n > (1 << 23)) return BTO_ERR_INVALID_ARG;
             B.n[a] = n;
             B.nn[a] = n + 1;
             B.S[a] = (n + s - 1) / s;

@@ -111,7 +111,7 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
     int64_t nodes = 1;
     for (int a = 0; a < 3; ++a) {
         const int32_t n = extent_cells[a];
-        if (n < 1 || n > (1 << 24) || !std::isfinite(origin[a]) || !finite_pos(spacing[a]))
+        if (n < 1 || n > (1 << 23) || !std::isfinite(origin[a]) || !finite_pos(spacing[a]))
             return BTO_ERR_INVALID_ARG;
         B.n[a] = n;
         B.nn[a] = n + 1;

@@ -119,30 +119,29 @@ struct BoxSrc {
     int ry, pitch;
     uint32_t d0, dy, dz;          // F3 row offsets: (d0 + j dy + k dz) mod 4 floats
 
-    __device__ __forceinline__ void load(int ix, int iy, int iz, float (&v)[8][3]) const {
+    __device__ __forceinline__ void load(int ix, int iy, int iz, uint32_t node, PCell &C) const {
         if (ix >= x0 && ix < x1 && iy >= y0 && iy < y1 && iz >= z0 && iz < z1) {
             const int j = iy - y0, k = iz - z0, xo = ix - x0;
+            float e[4][6];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int q = 0; q < 4; ++q) {
+                const int b = q & 1, c = q >> 1;
+                const int row = (j + b) + ry * (k + c);
+                if (LAYOUT == LAYOUT_F4) {
+                    const float4 *p = reinterpret_cast<const float4 *>(sm + row * pitch) + xo;
+                    const float4 a0 = p[0], a1 = p[1];
+                    e[q][0] = a0.x; e[q][1] = a0.y; e[q][2] = a0.z;
+                    e[q][3] = a1.x; e[q][4] = a1.y; e[q][5] = a1.z;
+                } else {
+                    const uint32_t d = (d0 + (uint32_t)(j + b) * dy + (uint32_t)(k + c) * dz) & 3u;
+                    const float *p = sm + row * pitch + d + 3 * xo;
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int row = (j + b) + ry * (k + c);
-                    const int k0 = 2 * b + 4 * c;
-                    if (LAYOUT == LAYOUT_F4) {
-                        const float4 *p = reinterpret_cast<const float4 *>(sm + row * pitch) + xo;
-                        const float4 a0 = p[0], a1 = p[1];
-                        v[k0][0] = a0.x; v[k0][1] = a0.y; v[k0][2] = a0.z;
-                        v[k0 + 1][0] = a1.x; v[k0 + 1][1] = a1.y; v[k0 + 1][2] = a1.z;
-                    } else {
-                        const uint32_t d = (d0 + (uint32_t)(j + b) * dy + (uint32_t)(k + c) * dz) & 3u;
-                        const float *p = sm + row * pitch + d + 3 * xo;
-                        v[k0][0] = p[0]; v[k0][1] = p[1]; v[k0][2] = p[2];
-                        v[k0 + 1][0] = p[3]; v[k0 + 1][1] = p[4]; v[k0 + 1][2] = p[5];
-                    }
+                    for (int m = 0; m < 6; ++m) e[q][m] = p[m];
                 }
             }
+            pcell_set(C, e[0], e[1], e[2], e[3]);
         } else {
-            load_cell<LAYOUT>(field, nnx, nnxy, ix, iy, iz, v);
+            load_pcell_global<LAYOUT>(field, nnx, nnxy, node, C);
         }
     }
 };
