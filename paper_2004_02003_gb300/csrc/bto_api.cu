@@ -58,24 +58,22 @@ struct bto_ctx {
     float4 *f4buf[2] = {nullptr, nullptr};
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ing_done[2] = {nullptr, nullptr}, adv_done[2] = {nullptr, nullptr};
-    // tiled advection (K3t): tile buckets, overflow region, rotating counts
+    // tiled advection (K3t): per-tile front and move-in regions, overflow region, rotating counts
     bool tiled = false;
     int32_t tdim[3] = {0, 0, 0};
     int tnt = 128, tgrid = 0, tocc = 0;
     size_t tsmem = 0;
-    int32_t tpitch = 0, tbox = 0, tbuf = 0, tnbuf = 2, tcap_max = 0, tstage_rec = 1;
+    int32_t tpitch = 0, tbox = 0, tbuf = 0, tnbuf = 2, tcap_max = 0, tcm = 0;
     int32_t ntiles = 0;
-    int64_t obase = 0, tslots = 0;
+    int64_t mbase = 0, obase = 0, tslots = 0;
     int tiling_gen = 0;
     bto::TileDev *tiles = nullptr;
     bto::BlockTiles *btiles = nullptr;
-    int32_t *unit_tile = nullptr;   // [obase/32] tile of each 32-slot unit of the buckets
+    int32_t *unit_tile = nullptr;   // [mbase/32] tile of each 32-slot unit of the front regions
     int32_t *tseed = nullptr;       // [P] global id of the i-th seed
     int64_t *tslot = nullptr;       // [P] its slot
     int32_t *tcnt0 = nullptr;       // [ntiles] seeds per tile
-    int32_t *tcap = nullptr;        // [ntiles] bucket capacity (lim at seeding)
     int32_t *tfront[2] = {nullptr, nullptr};
-    int32_t *tlim[2] = {nullptr, nullptr};
     int32_t *tmv[3] = {nullptr, nullptr, nullptr};
     int32_t *ocnt = nullptr;        // [3] overflow counts
     float4 *tact[2] = {nullptr, nullptr};
@@ -167,11 +165,7 @@ void free_tiling(bto_ctx *c) {
     cudaFree(c->tseed);
     cudaFree(c->tslot);
     cudaFree(c->tcnt0);
-    cudaFree(c->tcap);
-    for (int k = 0; k < 2; ++k) {
-        cudaFree(c->tfront[k]);
-        cudaFree(c->tlim[k]);
-    }
+    for (int k = 0; k < 2; ++k) cudaFree(c->tfront[k]);
     for (int k = 0; k < 3; ++k) cudaFree(c->tmv[k]);
     cudaFree(c->ocnt);
     cudaFree(c->tact[0]);
@@ -182,8 +176,7 @@ void free_tiling(bto_ctx *c) {
     c->tseed = nullptr;
     c->tslot = nullptr;
     c->tcnt0 = nullptr;
-    c->tcap = nullptr;
-    for (int k = 0; k < 2; ++k) c->tfront[k] = c->tlim[k] = nullptr;
+    for (int k = 0; k < 2; ++k) c->tfront[k] = nullptr;
     for (int k = 0; k < 3; ++k) c->tmv[k] = nullptr;
     c->ocnt = nullptr;
     c->tact[0] = c->tact[1] = nullptr;
@@ -248,7 +241,7 @@ int aux_grid(const bto_ctx *c) {
 
 // Counts of the tiled list at the start of cycle c.
 bto::TileCounts tile_counts(const bto_ctx *c, int cyc) {
-    return bto::TileCounts{c->tfront[cyc & 1], c->tmv[cyc % 3], c->tlim[cyc & 1]};
+    return bto::TileCounts{c->tfront[cyc & 1], c->tmv[cyc % 3], c->ocnt + cyc % 3, c->mbase, c->obase, c->P, c->tcm};
 }
 
 int tiled_aux_grid(const bto_ctx *c) {
@@ -260,7 +253,6 @@ bto_status seed(bto_ctx *c, cudaStream_t s) {
         BTO_CUDA(bto::launch_seed_tiled(c->blocks, c->nb, c->tseed, c->tslot, c->P, c->tact[0], aux_grid(c), s));
         const size_t tb = sizeof(int32_t) * (size_t)c->ntiles;
         BTO_CUDA(cudaMemcpyAsync(c->tfront[0], c->tcnt0, tb, cudaMemcpyDeviceToDevice, s));
-        BTO_CUDA(cudaMemcpyAsync(c->tlim[0], c->tcap, tb, cudaMemcpyDeviceToDevice, s));
         for (int k = 0; k < 3; ++k) BTO_CUDA(cudaMemsetAsync(c->tmv[k], 0, tb, s));
         BTO_CUDA(cudaMemsetAsync(c->ocnt, 0, sizeof(int32_t) * 3, s));
         c->cycle = 0;
@@ -272,24 +264,20 @@ bto_status seed(bto_ctx *c, cudaStream_t s) {
     return BTO_OK;
 }
 
-// Launch configuration of the tiled kernel for the current layout: as many
-// staging buffers (2..4) as fit beside the CTAs that should share an SM
-// (four CTAs of 128 threads, two of 256).
+// Launch configuration of the tiled kernel for the current layout: one
+// CTA of 16 warps per SM (two of 8, four of 4), each with as many box
+// buffers (2..6) as fit in its share of the SM's shared memory.
 bto_status configure_tiled(bto_ctx *c) {
     const size_t box = bto::tiled_box_bytes(c->layout, c->tdim, &c->tpitch, &c->tbox);
     int optin = 0, per_sm = 0;
     BTO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     BTO_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
-    const int want_ctas = c->tnt == 128 ? 4 : 2;
+    const int want_ctas = std::max(1, 512 / c->tnt);
     const size_t room = std::min<size_t>((size_t)optin, (size_t)per_sm / want_ctas - 1024);
-    // records ride with the box when two such buffers fit
-    size_t buf = box + 16 * (size_t)c->tcap_max;
-    c->tstage_rec = bto::tiled_smem_bytes(buf, 2) <= room ? 1 : 0;
-    if (!c->tstage_rec) buf = box;
-    c->tbuf = (int32_t)(buf / 4);
-    int nbuf = 4;
-    while (nbuf > 2 && bto::tiled_smem_bytes(buf, nbuf) > room) --nbuf;
-    const size_t smem = bto::tiled_smem_bytes(buf, nbuf);
+    c->tbuf = (int32_t)(box / 4);
+    int nbuf = bto::tiled_max_buffers();
+    while (nbuf > 2 && bto::tiled_smem_bytes(box, nbuf) > room) --nbuf;
+    const size_t smem = bto::tiled_smem_bytes(box, nbuf);
     if (smem > (size_t)optin) return BTO_ERR_UNSUPPORTED;
     int occ = 0;
     BTO_CUDA(bto::tiled_prepare(c->layout, c->tnt, smem, &occ));
@@ -301,8 +289,11 @@ bto_status configure_tiled(bto_ctx *c) {
     return BTO_OK;
 }
 
-// Tiles of every block, the seeds' buckets (seeds of a tile in Morton order
-// of the block's lattice) and the device arrays of the tiled path.
+// Tiles of every block, the seeds' front regions (the seeds of a tile in
+// brick order of the block's lattice) and the device arrays of the tiled
+// path. Front capacity: the tile's seeds plus a quarter (at least 32),
+// rounded up to 32; move-in capacity: the same margin for the tile with the
+// most seeds, for every tile.
 bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     std::vector<bto::TileDev> tiles;
     std::vector<bto::BlockTiles> bt((size_t)c->nb);
@@ -323,8 +314,9 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
                         const int32_t c0 = k[a] * td[a], tn = std::min(td[a], B.n[a] - c0);
                         T.lo[a] = std::max(c0 - 1, 0);
                         T.hi[a] = std::min(c0 + tn + 1, B.n[a]);
+                        T.tlo[a] = (float)c0;
+                        T.thi[a] = k[a] + 1 < ntl[a] ? (float)(c0 + tn) : INFINITY;
                     }
-                    T.n0 = (int64_t)T.lo[0] + (int64_t)B.nn[0] * ((int64_t)T.lo[1] + (int64_t)B.nn[1] * T.lo[2]);
                     tiles.push_back(T);
                 }
     }
@@ -335,7 +327,7 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     for (int32_t b = 0; b < c->nb; ++b) {
         const BlockDev &B = c->blocks_h[(size_t)b];
         order.resize((size_t)B.nseeds);
-        morton_order(B.S, order.data());
+        brick_order(B.S, order.data());
         const bto::BlockTiles &T = bt[(size_t)b];
         for (int64_t m = 0; m < B.nseeds; ++m) {
             const int32_t p = order[(size_t)m];
@@ -347,24 +339,22 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
             ++count[(size_t)t];
         }
     }
-    int64_t base = 0;
-    for (int64_t t = 0; t < ntiles; ++t) {
-        const int32_t n0 = count[(size_t)t];
-        const int64_t cap = ((int64_t)n0 + std::max<int64_t>(n0 / 4, 32) + 31) / 32 * 32;
-        tiles[(size_t)t].cap = (int32_t)cap;
-        tiles[(size_t)t].base = base;
-        base += cap;
-    }
-    const int64_t obase = base, tslots = obase + c->P;
+    auto margin = [](int64_t n) { return (n + std::max<int64_t>(n / 4, 32) + 31) / 32 * 32; };
+    int64_t base = 0, seeds_max = 0;
     int32_t cap_max = 0;
-    std::vector<int32_t> caps((size_t)ntiles);
     for (int64_t t = 0; t < ntiles; ++t) {
-        caps[(size_t)t] = tiles[(size_t)t].cap;
-        cap_max = std::max(cap_max, tiles[(size_t)t].cap);
+        const int64_t capf = margin(count[(size_t)t]);
+        tiles[(size_t)t].capf = (int32_t)capf;
+        tiles[(size_t)t].fbase = base;
+        base += capf;
+        cap_max = std::max(cap_max, (int32_t)capf);
+        seeds_max = std::max<int64_t>(seeds_max, count[(size_t)t]);
     }
-    std::vector<int32_t> unit_tile((size_t)(obase / bto::kUnit));
+    const int64_t cm = margin(seeds_max) - seeds_max;
+    const int64_t mbase = base, obase = mbase + ntiles * cm, tslots = obase + c->P;
+    std::vector<int32_t> unit_tile((size_t)(mbase / bto::kUnit));
     for (int64_t t = 0; t < ntiles; ++t)
-        for (int64_t u = tiles[(size_t)t].base / bto::kUnit; u < (tiles[(size_t)t].base + tiles[(size_t)t].cap) / bto::kUnit; ++u)
+        for (int64_t u = tiles[(size_t)t].fbase / bto::kUnit; u < (tiles[(size_t)t].fbase + tiles[(size_t)t].capf) / bto::kUnit; ++u)
             unit_tile[(size_t)u] = (int32_t)t;
     std::vector<int32_t> fill((size_t)ntiles, 0);
     std::vector<int32_t> tseed((size_t)c->P);
@@ -372,17 +362,18 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     for (int32_t b = 0; b < c->nb; ++b) {
         const BlockDev &B = c->blocks_h[(size_t)b];
         order.resize((size_t)B.nseeds);
-        morton_order(B.S, order.data());
+        brick_order(B.S, order.data());
         for (int64_t m = 0; m < B.nseeds; ++m) {
             const int64_t i = B.base + m;
             const int32_t t = tile_of[(size_t)i];
             tseed[(size_t)i] = (int32_t)(B.base + order[(size_t)m]);
-            tslot[(size_t)i] = tiles[(size_t)t].base + fill[(size_t)t]++;
+            tslot[(size_t)i] = tiles[(size_t)t].fbase + fill[(size_t)t]++;
         }
     }
 
     free_tiling(c);
     c->ntiles = (int32_t)ntiles;
+    c->mbase = mbase;
     c->obase = obase;
     c->tslots = tslots;
     cudaError_t e = cudaMalloc(&c->tiles, sizeof(bto::TileDev) * (size_t)ntiles);
@@ -392,9 +383,7 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     if (e == cudaSuccess) e = cudaMalloc(&c->tslot, sizeof(int64_t) * (size_t)c->P);
     const size_t tb = sizeof(int32_t) * (size_t)ntiles;
     if (e == cudaSuccess) e = cudaMalloc(&c->tcnt0, tb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tcap, tb);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tfront[k], tb);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tlim[k], tb);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tmv[k], tb);
     if (e == cudaSuccess) e = cudaMalloc(&c->ocnt, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->tact[0], sizeof(float4) * (size_t)tslots);
@@ -406,11 +395,11 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     if (e == cudaSuccess) e = cudaMemcpy(c->tseed, tseed.data(), sizeof(int32_t) * (size_t)c->P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->tslot, tslot.data(), sizeof(int64_t) * (size_t)c->P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->tcnt0, count.data(), tb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->tcap, caps.data(), tb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { (void)cudaGetLastError(); free_tiling(c); return cuda_status(e); }
     for (int a = 0; a < 3; ++a) c->tdim[a] = td[a];
     c->tnt = nt;
     c->tcap_max = cap_max;
+    c->tcm = (int32_t)cm;
     c->tiled = true;
     bto_status st = configure_tiled(c);
     if (st != BTO_OK) { free_tiling(c); return st; }
@@ -573,16 +562,18 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
         a.fields = fields;
         a.in = c->tact[cyc & 1];
         a.out = c->tact[(cyc + 1) & 1];
-        a.cin = tile_counts(c, cyc);
+        a.front_in = c->tfront[cyc & 1];
         a.front_out = c->tfront[(cyc + 1) & 1];
-        a.lim_out = c->tlim[(cyc + 1) & 1];
+        a.movein_in = c->tmv[cyc % 3];
         a.movein_out = c->tmv[(cyc + 1) % 3];
         a.movein_zero = c->tmv[(cyc + 2) % 3];
         a.ocnt_in = c->ocnt + cyc % 3;
         a.ocnt_out = c->ocnt + (cyc + 1) % 3;
         a.ocnt_zero = c->ocnt + (cyc + 2) % 3;
+        a.mbase = c->mbase;
         a.obase = c->obase;
         a.ocap = c->P;
+        a.cm = c->tcm;
         a.term = c->term;
         a.clip = c->clip;
         a.err = c->derr;
@@ -596,7 +587,6 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
         a.pitch = c->tpitch;
         a.box_floats = c->tbox;
         a.buf_floats = c->tbuf;
-        a.stage_rec = c->tstage_rec;
         a.nbuf = c->tnbuf;
         a.inject_stall = c->inject_stall > 0 ? 1 : 0;
         if (c->inject_stall > 0) --c->inject_stall;
@@ -779,8 +769,8 @@ bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends, uint
     const int grid = aux_grid(ctx);
     if (ctx->tiled)
         BTO_CUDA(bto::launch_write_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[L & 1],
-                                              tile_counts(ctx, L), ctx->ocnt + L % 3, ctx->obase, ctx->P, d_ends,
-                                              d_valid, d_exit_cycle, tiled_aux_grid(ctx), s));
+                                              tile_counts(ctx, L), d_ends, d_valid, d_exit_cycle,
+                                              tiled_aux_grid(ctx), s));
     else
         BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, ctx->act[L & 1], ctx->gcnt[L & 1],
                                         ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
@@ -842,10 +832,10 @@ bto_status bto_set_tiling(bto_ctx *ctx, const int32_t tile_cells[3], int32_t thr
     for (int a = 0; a < 3; ++a)
         if (tile_cells[a] < 2 || tile_cells[a] > 128 || (tile_cells[a] & (tile_cells[a] - 1)))
             return BTO_ERR_INVALID_ARG;
-    if (threads_per_cta != 128 && threads_per_cta != 256) return BTO_ERR_INVALID_ARG;
+    if (threads_per_cta != 128 && threads_per_cta != 256 && threads_per_cta != 512) return BTO_ERR_INVALID_ARG;
     if (ctx->ingest) return BTO_ERR_STATE;
-    // every thread issues at most four copies per tile: staged rows + 2 record ranges
-    if ((int64_t)(tile_cells[1] + 3) * (tile_cells[2] + 3) + 2 > 4 * (int64_t)threads_per_cta)
+    // each lane stages at most four rows of a tile's box
+    if ((int64_t)(tile_cells[1] + 3) * (tile_cells[2] + 3) > 4 * (int64_t)threads_per_cta)
         return BTO_ERR_UNSUPPORTED;
     int32_t pitch = 0, box = 0;
     int optin = 0;
@@ -876,7 +866,7 @@ bto_status bto_get_tiling(const bto_ctx *ctx, int32_t out[8]) {
     out[4] = ctx->tiled ? ctx->tgrid : 0;
     out[5] = ctx->tiled ? ctx->ntiles : 0;
     out[6] = ctx->tiled ? ctx->tnbuf : 0;
-    out[7] = ctx->tiled ? ctx->tstage_rec : 0;
+    out[7] = ctx->tiled ? 1 : 0;   // particle records are staged with the box
     return BTO_OK;
 }
 
@@ -958,8 +948,7 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
         if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)std::max<int64_t>(ctx->nb, ctx->slots / 32)));
         BTO_CUDA(cudaMemsetAsync(ctx->diag_dst, 0, sizeof(int64_t) * (size_t)ctx->nb, s));
         BTO_CUDA(bto::launch_count_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[cyc & 1],
-                                              tile_counts(ctx, cyc), ctx->ocnt + cyc % 3, ctx->obase, ctx->P,
-                                              ctx->diag_dst, tiled_aux_grid(ctx), s));
+                                              tile_counts(ctx, cyc), ctx->diag_dst, tiled_aux_grid(ctx), s));
         std::vector<int64_t> cnt((size_t)ctx->nb), start((size_t)ctx->nb);
         BTO_CUDA(cudaMemcpyAsync(cnt.data(), ctx->diag_dst, sizeof(int64_t) * (size_t)ctx->nb, cudaMemcpyDeviceToHost, s));
         BTO_CUDA(cudaStreamSynchronize(s));
@@ -969,8 +958,8 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
         }
         BTO_CUDA(cudaMemcpyAsync(ctx->diag_dst, start.data(), sizeof(int64_t) * (size_t)ctx->nb, cudaMemcpyHostToDevice, s));
         BTO_CUDA(bto::launch_gather_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[cyc & 1],
-                                               tile_counts(ctx, cyc), ctx->ocnt + cyc % 3, ctx->obase, ctx->P,
-                                               ctx->diag_dst, reinterpret_cast<float4 *>(d_out), tiled_aux_grid(ctx), s));
+                                               tile_counts(ctx, cyc), ctx->diag_dst, reinterpret_cast<float4 *>(d_out),
+                                               tiled_aux_grid(ctx), s));
         BTO_CUDA(cudaStreamSynchronize(s));
         return BTO_OK;
     }

@@ -53,17 +53,21 @@ struct AdvectArgs {
 enum { LAYOUT_F3 = 0, LAYOUT_F4 = 1 };
 
 // Tiled advection (kernel K3t). Each block's cells are cut into tiles of
-// tx * ty * tz cells (ragged at the upper faces). A tile owns a bucket of
-// list slots [base, base + cap); the live particles whose cell lies in the
-// tile at the start of a cycle fill its first cnt slots. Particles whose
-// bucket is full go to an overflow region shared by all blocks.
+// tx * ty * tz cells (powers of two; ragged at the upper faces). The live
+// particles whose cell lies in tile t at the start of a cycle sit in two
+// regions of the list: the front region [fbase, fbase + capf), holding the
+// particles that stayed in t during the last cycle (or its seeds), and the
+// move-in region [mbase + t * cm, + cm), holding those that came from other
+// tiles. Records that find their region full go to an overflow region
+// shared by all blocks, [obase, obase + ocap).
 struct TileDev {
     int32_t b;          // block
-    int32_t cap;        // bucket capacity (multiple of 32)
-    int64_t base;       // first slot of the bucket (multiple of 32)
+    int32_t capf;       // front-region capacity (multiple of 32)
+    int64_t fbase;      // first slot of the front region (multiple of 32)
     int32_t lo[3];      // staged node box: first node per axis (first cell - 1, clamped)
     int32_t hi[3];      // last node per axis (last cell + 2, clamped to n)
-    int64_t n0;         // node index of lo in the block's field
+    float tlo[3];       // first cell of the tile per axis
+    float thi[3];       // first cell after the tile; +inf on the block's last tile of the axis
 };
 
 struct BlockTiles {
@@ -71,22 +75,23 @@ struct BlockTiles {
     int32_t nt[3];      // tiles per axis (x fastest)
 };
 
-// Per-tile counts of a tiled list. The home CTA of tile t writes its
-// surviving particles to the front of the bucket, [base, base + front[t]);
-// particles that move in from other tiles are appended from the back,
-// [base + cap - m, base + cap) with m = min(movein[t], lim[t]), where lim[t]
-// = cap - (particles of t when they moved), so the two ends never meet.
+// Counts of a tiled list, as the interval-end and diagnostic kernels read
+// them: per tile its front count and move-in count, and the overflow count.
 struct TileCounts {
     const int32_t *front;
     const int32_t *movein;
-    const int32_t *lim;
+    const int32_t *ocnt;
+    int64_t mbase;       // first slot of the move-in regions
+    int64_t obase;       // first slot of the overflow region
+    int64_t ocap;        // overflow capacity
+    int32_t cm;          // move-in capacity per tile
 };
 
-// Arguments of one tiled cycle. front and lim are written (plain stores) for
-// every tile every cycle and ping-pong; movein counts are atomic and rotate
+// Arguments of one tiled cycle. Front counts are written (plain stores) for
+// every tile every cycle and ping-pong; move-in counts are atomic and rotate
 // over three arrays (cycle c reads one, appends to the next and clears the
-// third). Overflow counts rotate likewise. List records are (xi, global id
-// bits). Tile extents are powers of two (tsh = log2).
+// third), as do the overflow counts. List records are (xi, global id bits).
+// Tile extents are powers of two (tsh = log2).
 struct TiledArgs {
     const BlockDev *blocks;
     const BlockTiles *btiles;
@@ -97,16 +102,18 @@ struct TiledArgs {
     const void *const *fields;   // device array [nb] used when field == NULL
     const float4 *in;
     float4 *out;
-    TileCounts cin;              // counts of the input list
+    const int32_t *front_in;
     int32_t *front_out;
-    int32_t *lim_out;
+    const int32_t *movein_in;
     int32_t *movein_out;
     int32_t *movein_zero;
     const int32_t *ocnt_in;      // overflow counts (one int each)
     int32_t *ocnt_out;
     int32_t *ocnt_zero;
+    int64_t mbase;               // first slot of the move-in regions
     int64_t obase;               // first slot of the overflow region
     int64_t ocap;                // its capacity (all particles)
+    int32_t cm;                  // move-in capacity per tile
     float4 *term;
     float4 *clip;
     int32_t *err;                // set to 1 when a bounded wait gives up
@@ -115,10 +122,9 @@ struct TiledArgs {
     int32_t tsh[3];              // log2 of the tile extent per axis
     int32_t pitch;               // floats per staged node row
     int32_t box_floats;          // floats of a staged box
-    int32_t buf_floats;          // floats per staging buffer (box, then up to cap_max records)
-    int32_t stage_rec;           // 1: particle records staged with the box; 0: read from the list
-    int32_t nbuf;                // staging buffers (2..4)
-    int32_t inject_stall;        // test hook: CTA 0's first staging barrier never completes
+    int32_t buf_floats;          // floats per staging buffer (a tile's box)
+    int32_t nbuf;                // staging buffers (2..6)
+    int32_t inject_stall;        // test hook: CTA 0's first staged tile never completes
 };
 
 // Kernel launchers (bto_kernels.cu). Each returns cudaGetLastError().
@@ -131,23 +137,23 @@ cudaError_t advect_occupancy(int layout, int nt, int ppt, bool cap, bool batched
 size_t tiled_box_bytes(int layout, const int32_t tdim[3], int32_t *pitch, int32_t *box_floats);
 // Dynamic shared memory of a CTA with nbuf staging buffers of buffer_bytes.
 size_t tiled_smem_bytes(size_t buffer_bytes, int nbuf);
-// nt = threads per CTA (128 or 256); ctas_per_sm = resident CTAs at smem.
+// nt = threads per CTA (128, 256 or 512); ctas_per_sm = resident CTAs at smem.
 cudaError_t tiled_prepare(int layout, int nt, size_t smem, int *ctas_per_sm);
+// Largest number of box buffers a CTA of the tiled kernel can hold.
+int tiled_max_buffers();
 cudaError_t launch_advect_tiled(const TiledArgs &a, int layout, int nt, int grid, size_t smem,
                                 cudaStream_t s);
 cudaError_t launch_seed_tiled(const BlockDev *blocks, int32_t nb, const int32_t *tseed,
                               const int64_t *tslot, int64_t P, float4 *act, int grid, cudaStream_t s);
 cudaError_t launch_write_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
                                     const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                    const int32_t *ocnt, int64_t obase, int64_t ocap, float *ends,
-                                    uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s);
+                                    float *ends, uint8_t *valid, int32_t *exit_cycle, int grid,
+                                    cudaStream_t s);
 cudaError_t launch_gather_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
                                      const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                     const int32_t *ocnt, int64_t obase, int64_t ocap,
                                      int64_t *cursor, float4 *out, int grid, cudaStream_t s);
 cudaError_t launch_count_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
                                     const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                    const int32_t *ocnt, int64_t obase, int64_t ocap,
                                     int64_t *per_block, int grid, cudaStream_t s);
 
 cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,

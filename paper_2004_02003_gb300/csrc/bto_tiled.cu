@@ -5,28 +5,36 @@
 // Sec. 3.1 and Sec. 3.3; terminated particles leave the live set, Sec. 3.1's
 // particle management), organised around the field instead of the particles:
 //
-//  * each block's cells are cut into tiles; a tile's particles sit in its
-//    bucket of list slots;
-//  * a persistent CTA takes tiles in turn. For each it stages, with bulk
-//    asynchronous copies (cp.async.bulk, completion on an mbarrier), the
-//    nodes of the tile plus one cell of halo on every side (the step of a
-//    particle moving at most one cell per step stays inside) and the tile's
-//    particle records into one buffer of a ring of shared-memory buffers,
-//    nbuf tiles ahead of the one being advected;
+//  * each block's cells are cut into tiles; the live particles whose cell
+//    lies in a tile at the start of a cycle sit in that tile's two list
+//    regions: its front region (the survivors that stayed in the tile) and
+//    its move-in region (the survivors that came from other tiles);
+//  * a persistent CTA takes the tiles t = blockIdx.x, + gridDim.x, ... One
+//    producer warp stages, with bulk asynchronous copies (cp.async.bulk,
+//    completion counted in bytes on an mbarrier), the nodes of a tile plus
+//    one cell of halo on every side and the tile's particle records into
+//    one buffer of a ring of shared-memory buffers, while the consumer
+//    warps advect the tiles staged before it. Full and empty mbarriers hand
+//    the buffers back and forth; there is no CTA-wide barrier in the loop;
 //  * the corners of a cell are read from shared memory; a cell outside the
 //    staged box (a particle faster than one cell per step, or one in the
 //    overflow region) is gathered from global memory, so results do not
 //    depend on the tiling;
-//  * a survivor still in its tile is written to the front of the tile's
-//    next bucket (positions from a shared-memory counter); one that moved
-//    to another tile is appended from the back of that tile's bucket
-//    (warp-aggregated global atomics; see TileCounts); a full bucket sends
-//    it to the overflow region, which the CTAs advect after the tiles.
+//  * a survivor still in its tile is written to the tile's next front
+//    region (position from a shared-memory counter); one that moved to
+//    another tile is appended to that tile's next move-in region (one
+//    global atomic on the destination's counter); a full region sends it
+//    to the overflow region, which the CTAs advect after the tiles.
 //
 // Staged rows: the F3 node row [x0, x1] of (y, z) is copied as the 16-byte
 // aligned span that contains it; its first node then sits d = (field_word +
 // 3 * node) mod 4 floats into the row's buffer. Reading the 16-byte chunks
 // that hold field bytes never leaves the field's pages.
+//
+// Every wait is bounded: a wait that gives up after about two seconds of SM
+// clock raises the context's error word and the CTA's abort flag, after
+// which the CTA stops, waits (again bounded) for its copies in flight and
+// leaves the tiles it has not finished empty and consistent.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -39,7 +47,6 @@ namespace {
 using namespace dev;
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxBuf = 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -83,21 +90,33 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait for a phase: gives up after about two seconds of SM clock, or
-// as soon as another warp of the CTA has given up (abort flag); the first to
-// give up raises the context's error word.
+// About two seconds of SM clock.
+constexpr long long kWaitCycles = 1ll << 32;
+
+// Bounded wait for a phase inside the tile loop: gives up when the CTA's
+// abort flag is up, or after kWaitCycles, in which case it raises both the
+// abort flag and the context's error word.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *err) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > (1ll << 32)) {
+        if (clock64() - t0 > kWaitCycles) {
             *abort_flag = 1;
             atomicExch(err, 1);
             return false;
         }
     }
     return true;
+}
+
+// Bounded wait used after an abort, for copies still in flight: it ignores
+// the abort flag, so it waits up to the full bound for a phase that can
+// still complete.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return;
 }
 
 __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, int nb, int64_t i) {
@@ -109,31 +128,36 @@ __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, i
     return lo;
 }
 
+__device__ __forceinline__ const void *block_field(const TiledArgs &a, int b) {
+    return a.field ? a.field : a.fields[b];
+}
+
 // Cell source over a staged box, with the global gather as fallback.
 template <int LAYOUT>
 struct BoxSrc {
     const float *sm;
     const void *field;
     uint32_t nnx, nnxy;
-    int x0, y0, z0, x1, y1, z1;   // staged nodes [x0, x1] x [y0, y1] x [z0, z1]
-    int ry, pitch;
-    uint32_t d0, dy, dz;          // F3 row offsets: (d0 + j dy + k dz) mod 4 floats
+    int lox, loy, loz;
+    uint32_t cx, cy, cz;   // cells of the box per axis (staged nodes - 1)
+    int my, pitch;         // rows per z plane, floats per row
+    uint32_t d0, dy, dz;   // F3 row misalignment: (d0 + j dy + k dz) mod 4 floats
 
     __device__ __forceinline__ void load(int ix, int iy, int iz, uint32_t node, PCell &C) const {
-        if (ix >= x0 && ix < x1 && iy >= y0 && iy < y1 && iz >= z0 && iz < z1) {
-            const int j = iy - y0, k = iz - z0, xo = ix - x0;
+        const uint32_t xo = (uint32_t)(ix - lox), j = (uint32_t)(iy - loy), k = (uint32_t)(iz - loz);
+        if (xo < cx && j < cy && k < cz) {
+            const int r = (int)j + my * (int)k;
             float e[4][6];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int b = q & 1, c = q >> 1;
-                const int row = (j + b) + ry * (k + c);
+                const int row = r + (q & 1) + ((q & 2) ? my : 0);
                 if (LAYOUT == LAYOUT_F4) {
                     const float4 *p = reinterpret_cast<const float4 *>(sm + row * pitch) + xo;
                     const float4 a0 = p[0], a1 = p[1];
                     e[q][0] = a0.x; e[q][1] = a0.y; e[q][2] = a0.z;
                     e[q][3] = a1.x; e[q][4] = a1.y; e[q][5] = a1.z;
                 } else {
-                    const uint32_t d = (d0 + (uint32_t)(j + b) * dy + (uint32_t)(k + c) * dz) & 3u;
+                    const uint32_t d = (d0 + (j + (q & 1)) * dy + (k + (q >> 1)) * dz) & 3u;
                     const float *p = sm + row * pitch + d + 3 * xo;
 #pragma unroll
                     for (int m = 0; m < 6; ++m) e[q][m] = p[m];
@@ -146,79 +170,95 @@ struct BoxSrc {
     }
 };
 
-__device__ __forceinline__ const void *block_field(const TiledArgs &a, int b) {
-    return a.field ? a.field : a.fields[b];
-}
+// A non-empty tile of the CTA's sequence t = blockIdx.x + k * gridDim.x.
+struct TileView {
+    int t;        // tile
+    int nf, nm;   // records in its front part and in its move-in part
+};
 
-// Particles of tile t (bucket capacity cap) in a list with counts c: front
-// part, then back part. The counts are clamped to the bucket, so that no
-// access leaves it whatever the counts hold.
-__device__ __forceinline__ void tile_parts(const TileCounts &c, int t, int cap, int *nf, int *nm) {
-    const int f = min(max(__ldcg(c.front + t), 0), cap);
-    *nf = f;
-    *nm = min(max(min(__ldcg(c.movein + t), __ldcg(c.lim + t)), 0), cap - f);
-}
+// A warp's walk over the CTA's tiles, skipping the empty ones. The lanes
+// hold the counts of a window of 32 consecutive tiles of the sequence;
+// `left` marks the non-empty ones not yet returned. Every warp of the CTA
+// walks the same sequence and sees the same tiles.
+struct TileWalk {
+    int k0;          // sequence index of the window's first tile
+    unsigned left;   // non-empty tiles of the window not yet returned
+    int nf, nm;      // counts of this lane's tile of the window
+};
 
-
-// Issue the copies of tile t (its staged box, then its particle records:
-// front part, back part) into buffer dst; every thread arrives once on bar
-// with the bytes of the copies it issued. A tile without particles copies
-// nothing (the phase completes on the arrivals alone).
-template <int LAYOUT, int NT>
-__device__ __forceinline__ void stage_tile(const TiledArgs &a, int t, float *dst, uint32_t bar) {
-    const TileDev T = a.tiles[t];
-    int nf, nm;
-    tile_parts(a.cin, t, T.cap, &nf, &nm);
-    if (nf + nm == 0) {
-        mbar_arrive(bar);
-        return;
+__device__ __forceinline__ void walk_load(const TiledArgs &a, TileWalk &w, bool write_empty) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x + (w.k0 + lane) * (int)gridDim.x;
+    w.nf = 0;
+    w.nm = 0;
+    if (t < a.ntiles) {
+        w.nf = min(max(__ldcg(a.front_in + t), 0), __ldg(&a.tiles[t].capf));
+        w.nm = min(max(__ldcg(a.movein_in + t), 0), a.cm);
+        // an empty tile holds no survivor at the end of the cycle either
+        if (write_empty && w.nf + w.nm == 0) a.front_out[t] = 0;
     }
+    w.left = __ballot_sync(kFull, w.nf + w.nm > 0);
+}
+
+__device__ __forceinline__ void walk_init(const TiledArgs &a, TileWalk &w, bool write_empty) {
+    w.k0 = 0;
+    walk_load(a, w, write_empty);
+}
+
+// Next non-empty tile of the walk; false at the end of the sequence.
+__device__ __forceinline__ bool walk_next(const TiledArgs &a, TileWalk &w, TileView &v, bool write_empty) {
+    const int G = gridDim.x;
+    while (w.left == 0) {
+        w.k0 += 32;
+        if (blockIdx.x + w.k0 * G >= a.ntiles) return false;
+        walk_load(a, w, write_empty);
+    }
+    const int p = __ffs(w.left) - 1;
+    w.left &= w.left - 1;
+    v.t = blockIdx.x + (w.k0 + p) * G;
+    v.nf = __shfl_sync(kFull, w.nf, p);
+    v.nm = __shfl_sync(kFull, w.nm, p);
+    return true;
+}
+
+// This warp's share of the copies of tile v into buffer dst: the box rows
+// r with r mod nwarps == warp, one per lane. Every lane arrives once on the
+// full barrier, announcing the bytes of its own copies first.
+template <int LAYOUT>
+__device__ __forceinline__ void stage_share(const TiledArgs &a, const TileView &v, float *dst, uint32_t bar,
+                                            int warp, int nwarps, bool stall) {
+    const int lane = threadIdx.x & 31;
+    const TileDev &T = a.tiles[v.t];
     const BlockDev &B = a.blocks[T.b];
     const uint64_t nnx = (uint64_t)B.nn[0], nnxy = (uint64_t)B.nn[0] * (uint64_t)B.nn[1];
-    const int ry = T.hi[1] - T.lo[1] + 1, rows = ry * (T.hi[2] - T.lo[2] + 1);
-    const float inv_ry = 1.f / (float)ry;
+    const int m0 = T.hi[0] - T.lo[0] + 1, m1 = T.hi[1] - T.lo[1] + 1, m2 = T.hi[2] - T.lo[2] + 1;
     const uint64_t esz = LAYOUT == LAYOUT_F4 ? 16 : 12;
-    const uint64_t mx = (uint64_t)(T.hi[0] - T.lo[0] + 1);
-    const uintptr_t fbase = reinterpret_cast<uintptr_t>(block_field(a, T.b)) + esz * (uint64_t)T.n0;
-    float *rec = dst + a.box_floats;
-    // copy r < rows: staged row r; r == rows, rows + 1: the record ranges.
-    // First the bytes this thread will copy (announced on the barrier with
-    // its arrival), then the copies.
-    auto span = [&](int r, uintptr_t &src, uint32_t &sdst) -> uint32_t {
-        if (r < rows) {
-            const int k = (int)(((float)r + 0.5f) * inv_ry);
-            const int jy = r - k * ry;
-            const uintptr_t lo = fbase + esz * (nnx * (uint64_t)jy + nnxy * (uint64_t)k);
-            src = lo & ~(uintptr_t)15;
-            sdst = smem_u32(dst + (size_t)r * a.pitch);
-            return (uint32_t)(((lo + esz * mx + 15) & ~(uintptr_t)15) - src);
-        }
-        if (r == rows) {
-            src = reinterpret_cast<uintptr_t>(a.in + T.base);
-            sdst = smem_u32(rec);
-            return 16u * (uint32_t)nf;
-        }
-        src = reinterpret_cast<uintptr_t>(a.in + T.base + T.cap - nm);
-        sdst = smem_u32(rec + 4 * nf);
-        return 16u * (uint32_t)nm;
-    };
-    const int ncopies = rows + (a.stage_rec ? 2 : 0);
+    const uint64_t n0 = (uint64_t)T.lo[0] + nnx * (uint64_t)T.lo[1] + nnxy * (uint64_t)T.lo[2];
+    const uintptr_t fbase = reinterpret_cast<uintptr_t>(a.field ? a.field : a.fields[T.b]) + esz * n0;
+    const int rows = m1 * m2;
     uint32_t bytes = 0;
-    for (int r = threadIdx.x; r < ncopies; r += NT) {
-        uintptr_t src;
-        uint32_t sdst;
-        bytes += span(r, src, sdst);
+    uintptr_t src[4];
+    uint32_t sdst[4], n[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = warp + nwarps * (lane + 32 * q);
+        n[q] = 0;
+        if (r < rows) {
+            const int k = r / m1, j = r - k * m1;
+            const uintptr_t lo = fbase + esz * (nnx * (uint64_t)j + nnxy * (uint64_t)k);
+            src[q] = lo & ~(uintptr_t)15;
+            sdst[q] = smem_u32(dst + (size_t)r * a.pitch);
+            n[q] = (uint32_t)(((lo + esz * (uint64_t)m0 + 15) & ~(uintptr_t)15) - src[q]);
+            bytes += n[q];
+        }
     }
-    // test hook: CTA 0 announces 16 bytes that no copy delivers, so that its
-    // bounded wait runs out (the error path of bto_test_wait_timeout)
-    if (a.inject_stall && blockIdx.x == 0 && threadIdx.x == 0) bytes += 16;
+    // test hook: announce 16 bytes that no copy delivers, so that the
+    // bounded wait on this buffer runs out (bto_test_wait_timeout)
+    if (stall && warp == 0 && lane == 0) bytes += 16;
     mbar_arrive_expect(bar, bytes);
-    for (int r = threadIdx.x; r < ncopies; r += NT) {
-        uintptr_t src;
-        uint32_t sdst;
-        const uint32_t n = span(r, src, sdst);
-        if (n) bulk_g2s(sdst, reinterpret_cast<const void *>(src), n, bar);
-    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (n[q]) bulk_g2s(sdst[q], reinterpret_cast<const void *>(src[q]), n[q], bar);
 }
 
 __device__ __forceinline__ void record_term(const TiledArgs &a, const float4 &r, int failed, float3 q) {
@@ -227,188 +267,236 @@ __device__ __forceinline__ void record_term(const TiledArgs &a, const float4 &r,
     if (a.clip) __stcs(a.clip + gid, make_float4(q.x, q.y, q.z, __int_as_float(failed)));
 }
 
-// Tile of a survivor's new cell (same block).
-__device__ __forceinline__ int dest_tile(const TiledArgs &a, const BlockTiles &bt, const Geo &g, float x, float y,
-                                         float z) {
-    const int ix = min(max(__float2int_rd(x), 0), g.nx - 1);
-    const int iy = min(max(__float2int_rd(y), 0), g.ny - 1);
-    const int iz = min(max(__float2int_rd(z), 0), g.nz - 1);
-    return bt.first + (ix >> a.tsh[0]) + bt.nt[0] * ((iy >> a.tsh[1]) + bt.nt[1] * (iz >> a.tsh[2]));
+__device__ __forceinline__ void append_overflow(const TiledArgs &a, const float4 &r) {
+    const int o = atomicAdd(a.ocnt_out, 1);
+    if ((int64_t)o < a.ocap) __stcs(a.out + a.obase + o, r);
 }
 
-// Survivors that left their tile (mover = true on the lanes concerned):
-// appended from the back of the destination bucket, beyond the particles
-// the destination holds this cycle; overflow when that room is used up.
-__device__ __forceinline__ void emit_movers(const TiledArgs &a, bool mover, int dest, const float4 &r) {
-    const unsigned mm = __ballot_sync(kFull, mover);
-    if (!mover) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(mm, dest);
-    const int leader = __ffs(peers) - 1;
-    int q = 0;
-    if (lane == leader) q = atomicAdd(a.movein_out + dest, __popc(peers));
-    q = __shfl_sync(peers, q, leader) + __popc(peers & ((1u << lane) - 1u));
-    const int cap = __ldg(&a.tiles[dest].cap);
-    int nf, nm;
-    tile_parts(a.cin, dest, cap, &nf, &nm);
-    if (q < cap - (nf + nm)) {
-        __stcs(a.out + __ldg(&a.tiles[dest].base) + (cap - 1 - q), r);
-    } else {
-        const int o = atomicAdd(a.ocnt_out, 1);
-        __stcs(a.out + a.obase + o, r);
-    }
-}
-
-// Advect the n particles of tile t from its staged buffer. Survivors in
-// the tile go to the front of its next bucket through the shared counter.
-template <int LAYOUT, int NT>
-__device__ __forceinline__ void advect_tile(const TiledArgs &a, int t, const float *buf, int nf, int n, int *scount,
-                                            int &cur_b, Geo &g, float3 &s, BlockTiles &bt, BoxSrc<LAYOUT> &src,
-                                            uint32_t &fw) {
-    const TileDev T = a.tiles[t];
-    if (T.b != cur_b) {
-        cur_b = T.b;
-        const BlockDev &B = a.blocks[cur_b];
-        g = load_geo(B);
-        s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
-        bt = a.btiles[cur_b];
-        src.field = block_field(a, cur_b);
-        src.nnx = g.nnx;
-        src.nnxy = g.nnxy;
-        fw = (uint32_t)(reinterpret_cast<uintptr_t>(src.field) >> 2);
-        src.dy = (3u * g.nnx) & 3u;
-        src.dz = (3u * g.nnxy) & 3u;
-    }
-    src.sm = buf;
-    src.x0 = T.lo[0]; src.y0 = T.lo[1]; src.z0 = T.lo[2];
-    src.x1 = T.hi[0]; src.y1 = T.hi[1]; src.z1 = T.hi[2];
-    src.ry = T.hi[1] - T.lo[1] + 1;
-    src.d0 = (fw + 3u * (uint32_t)T.n0) & 3u;
-    const float4 *rec = reinterpret_cast<const float4 *>(buf + a.box_floats);
-    const int lane = threadIdx.x & 31;
-    for (int i0 = 0; i0 < n; i0 += NT) {
-        const int i = i0 + threadIdx.x;
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool home = false, mover = false;
-        int dest = -1;
-        if (i < n) {
-            r = a.stage_rec ? rec[i] : __ldcs(a.in + T.base + (i < nf ? i : T.cap - n + i));
-            float3 x = make_float3(r.x, r.y, r.z), q;
-            const int failed = rk4_step_src(x, src, g, s, q);
-            if (failed == 0) {
-                r.x = x.x; r.y = x.y; r.z = x.z;
-                dest = dest_tile(a, bt, g, x.x, x.y, x.z);
-                home = dest == t;
-                mover = !home;
-            } else {
-                record_term(a, r, failed, q);
-            }
-        }
-        const unsigned hm = __ballot_sync(kFull, home);
-        if (hm) {
-            const int leader = __ffs(hm) - 1;
-            int pos = 0;
-            if (lane == leader) pos = atomicAdd(scount, __popc(hm));
-            pos = __shfl_sync(kFull, pos, leader) + __popc(hm & ((1u << lane) - 1u));
-            if (home) __stcs(a.out + T.base + pos, r);
-        }
-        emit_movers(a, mover, dest, r);
-    }
+// A survivor that left its tile: appended to the move-in region of the
+// tile of its new cell (same block), or to the overflow region.
+__device__ __forceinline__ void append_mover(const TiledArgs &a, const BlockTiles &bt, const Geo &g,
+                                             const float4 &r) {
+    int ix, iy, iz;
+    float f;
+    cell_coord(r.x, g.cmx, ix, f);
+    cell_coord(r.y, g.cmy, iy, f);
+    cell_coord(r.z, g.cmz, iz, f);
+    const int dest = bt.first + (ix >> a.tsh[0]) + bt.nt[0] * ((iy >> a.tsh[1]) + bt.nt[1] * (iz >> a.tsh[2]));
+    const int q = atomicAdd(a.movein_out + dest, 1);
+    if (q < a.cm) __stcs(a.out + a.mbase + (int64_t)dest * a.cm + q, r);
+    else append_overflow(a, r);
 }
 
 // Overflow particles: gathered from global memory (block from the id); every
-// survivor is a mover.
-template <int LAYOUT, int NT>
-__device__ void advect_overflow(const TiledArgs &a) {
+// survivor is a mover. Warp w of the grid takes particles w*32 + lane, ...
+template <int LAYOUT>
+__device__ void advect_overflow(const TiledArgs &a, int nwarps_cta) {
     const int64_t n = min(max((int64_t)__ldcg(a.ocnt_in), (int64_t)0), a.ocap);
-    for (int64_t i0 = (int64_t)blockIdx.x * NT; i0 < n; i0 += (int64_t)gridDim.x * NT) {
-        const int64_t i = i0 + threadIdx.x;
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool mover = false;
-        int dest = -1;
-        if (i < n) {
-            r = __ldcs(a.in + a.obase + i);
-            const int b = a.nb == 1 ? 0 : find_block(a.blocks, a.nb, __float_as_int(r.w));
-            const BlockDev &B = a.blocks[b];
-            const Geo g = load_geo(B);
-            const float3 s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
-            float3 x = make_float3(r.x, r.y, r.z), q;
-            const int failed = rk4_step<LAYOUT>(x, block_field(a, b), g, s, q);
-            if (failed == 0) {
-                r.x = x.x; r.y = x.y; r.z = x.z;
-                mover = true;
-                dest = dest_tile(a, a.btiles[b], g, x.x, x.y, x.z);
-            } else {
-                record_term(a, r, failed, q);
-            }
+    const int64_t w = (int64_t)blockIdx.x * nwarps_cta + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * nwarps_cta * 32;
+    for (int64_t i = w * 32 + (threadIdx.x & 31); i < n; i += stride) {
+        float4 r = __ldcs(a.in + a.obase + i);
+        const int b = a.nb == 1 ? 0 : find_block(a.blocks, a.nb, __float_as_int(r.w));
+        const BlockDev &B = a.blocks[b];
+        const Geo g = load_geo(B);
+        const float3 s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
+        float3 x = make_float3(r.x, r.y, r.z), q;
+        const int failed = rk4_step<LAYOUT>(x, block_field(a, b), g, s, q);
+        if (failed == 0) {
+            r.x = x.x; r.y = x.y; r.z = x.z;
+            append_mover(a, a.btiles[b], g, r);
+        } else {
+            record_term(a, r, failed, q);
         }
-        emit_movers(a, mover, dest, r);
     }
 }
 
-template <int LAYOUT, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) advect_tiled_kernel(const TiledArgs a) {
+// Shared memory of a CTA after its nbuf box buffers of buf_floats floats:
+// barriers, per-buffer survivor counters and tiles, the abort flag.
+constexpr int kMaxBufs = 6;
+struct SmemTail {
+    unsigned long long full[kMaxBufs];
+    unsigned long long empty[kMaxBufs];
+    int scount[kMaxBufs];
+    int tile[kMaxBufs];
+    int abort_flag;
+};
+
+// Every warp of the CTA walks the CTA's tiles in the same order, issues its
+// share of the copies of the tile nbuf - 1 ahead, and advects its share of
+// the particles of the current tile. Buffer of the j-th tile: j mod nbuf;
+// its full and empty phases have parity (j / nbuf) & 1. Warp 0 also writes
+// each tile's front count once every warp has finished the tile.
+template <int LAYOUT, int NW, int MINB>
+__global__ void __launch_bounds__(32 * NW, MINB) advect_tiled_kernel(const TiledArgs a) {
+    // Programmatic dependent launch: nothing is read or written before the
+    // previous cycle's grid has completed and its writes are visible.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(128) float tsm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tsm + (size_t)a.nbuf * a.buf_floats);
-    const uint32_t full0 = smem_u32(bars);
-    int *scount = reinterpret_cast<int *>(bars + kMaxBuf);
+    SmemTail *tail = reinterpret_cast<SmemTail *>(tsm + (size_t)a.nbuf * a.buf_floats);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NB = a.nbuf;
+    volatile int *abort_flag = &tail->abort_flag;
     if (threadIdx.x == 0) {
-        for (int k = 0; k < a.nbuf; ++k) mbar_init(full0 + 8u * k, NT);
-        *scount = 0;
+        for (int k = 0; k < NB; ++k) {
+            mbar_init(smem_u32(&tail->full[k]), 32 * NW);
+            mbar_init(smem_u32(&tail->empty[k]), NW);
+            tail->scount[k] = 0;
+        }
+        tail->abort_flag = 0;
         mbar_fence_init();
     }
-    // counts of the cycle after next start at zero
-    for (int t = blockIdx.x * NT + threadIdx.x; t < a.ntiles; t += gridDim.x * NT) a.movein_zero[t] = 0;
+    // move-in and overflow counts of the cycle after next start at zero
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += gridDim.x * blockDim.x) a.movein_zero[t] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.ocnt_zero = 0;
     __syncthreads();
 
-    const int G = gridDim.x;
-    for (int k = 0; k < a.nbuf; ++k) {
-        const int t = blockIdx.x + k * G;
-        if (t < a.ntiles) stage_tile<LAYOUT, NT>(a, t, tsm + (size_t)k * a.buf_floats, full0 + 8u * k);
+    const bool w0 = warp == 0;
+    bool stall = a.inject_stall && blockIdx.x == 0;
+    TileWalk sw, pw;
+    walk_init(a, sw, w0);
+    walk_init(a, pw, false);
+    int staged = 0;
+    for (; staged < NB - 1; ++staged) {
+        TileView v;
+        if (!walk_next(a, sw, v, w0)) break;
+        if (w0 && lane == 0) tail->tile[staged] = v.t;
+        stage_share<LAYOUT>(a, v, tsm + (size_t)staged * a.buf_floats, smem_u32(&tail->full[staged]), warp, NW, stall);
+        stall = false;
     }
+    bool more = staged == NB - 1;   // the staging walk may hold more tiles
+
     int cur_b = -1;
     Geo g{};
     float3 s = make_float3(0.f, 0.f, 0.f);
     BlockTiles bt{};
     BoxSrc<LAYOUT> src;
     src.pitch = a.pitch;
-    uint32_t fw = 0;
-    volatile int no_abort = 0;
-    for (int j = 0, t = blockIdx.x; t < a.ntiles; ++j, t += G) {
-        const int buf = j % a.nbuf;
-        const uint32_t bar = full0 + 8u * buf;
-        const bool ok = __syncthreads_and(mbar_wait(bar, (uint32_t)(j / a.nbuf) & 1u, &no_abort, a.err));
-        if (!ok) {
-            // the copies of the next tiles are already in flight: wait for
-            // them (bounded) before the CTA's shared memory is released
-            for (int k = 1; k < a.nbuf && t + k * G < a.ntiles; ++k)
-                mbar_wait(full0 + 8u * ((j + k) % a.nbuf), (uint32_t)((j + k) / a.nbuf) & 1u, &no_abort, a.err);
-            // this CTA's tiles, from the current one on, are left empty and
-            // consistent (their particles are lost; the error word says so)
-            for (int t2 = t + threadIdx.x * G; t2 < a.ntiles; t2 += NT * G) {
-                a.front_out[t2] = 0;
-                a.lim_out[t2] = __ldg(&a.tiles[t2].cap);
+    const unsigned lt = (1u << lane) - 1u;
+    int fin = 0;          // tiles whose front count warp 0 has written
+    int off = 0;          // chunks of 32 particles handed out so far, mod NW
+    int j = 0;
+    bool ok = true;
+    for (;; ++j) {
+        TileView v;
+        if (!walk_next(a, pw, v, false)) break;
+        const int b = j % NB;
+        if (!mbar_wait(smem_u32(&tail->full[b]), (uint32_t)(j / NB) & 1u, abort_flag, a.err)) { ok = false; break; }
+        const TileDev &T = a.tiles[v.t];
+        const int tb = T.b;
+        if (tb != cur_b) {
+            cur_b = tb;
+            const BlockDev &B = a.blocks[cur_b];
+            g = load_geo(B);
+            s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
+            bt = a.btiles[cur_b];
+            src.field = block_field(a, cur_b);
+            src.nnx = g.nnx;
+            src.nnxy = g.nnxy;
+            src.dy = (3u * g.nnx) & 3u;
+            src.dz = (3u * g.nnxy) & 3u;
+        }
+        src.sm = tsm + (size_t)b * a.buf_floats;
+        src.lox = T.lo[0]; src.loy = T.lo[1]; src.loz = T.lo[2];
+        src.cx = (uint32_t)(T.hi[0] - T.lo[0]); src.cy = (uint32_t)(T.hi[1] - T.lo[1]);
+        src.cz = (uint32_t)(T.hi[2] - T.lo[2]);
+        src.my = T.hi[1] - T.lo[1] + 1;
+        {
+            const uint64_t n0 = (uint64_t)T.lo[0] + g.nnx * ((uint64_t)T.lo[1] + (uint64_t)(g.nnxy / g.nnx) * T.lo[2]);
+            src.d0 = (uint32_t)((reinterpret_cast<uintptr_t>(src.field) >> 2) + 3ull * n0) & 3u;
+        }
+        const float tlx = T.tlo[0], tly = T.tlo[1], tlz = T.tlo[2];
+        const float thx = T.thi[0], thy = T.thi[1], thz = T.thi[2];
+        const int capf = T.capf;
+        const int64_t fbase = T.fbase;
+        const float4 *rin_f = a.in + fbase;
+        const float4 *rin_m = a.in + a.mbase + (int64_t)v.t * a.cm - v.nf;
+        const int n = v.nf + v.nm;
+        // chunks of 32 particles go to the warps in turn across tiles, so
+        // that a tile smaller than 32 * NW particles leaves the idle warps
+        // free to start on the next one
+        const int nch = (n + 31) >> 5;
+        for (int c = (warp - off + NW) % NW; c < nch; c += NW) {
+            const int i = c * 32 + lane;
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool home = false, mover = false;
+            if (i < n) {
+                r = __ldcs(i < v.nf ? rin_f + i : rin_m + i);
+                float3 x = make_float3(r.x, r.y, r.z), q;
+                const int failed = rk4_step_src(x, src, g, s, q);
+                if (failed == 0) {
+                    r.x = x.x; r.y = x.y; r.z = x.z;
+                    home = x.x >= tlx && x.x < thx && x.y >= tly && x.y < thy && x.z >= tlz && x.z < thz;
+                    mover = !home;
+                } else {
+                    record_term(a, r, failed, q);
+                }
             }
-            return;
+            const unsigned hm = __ballot_sync(kFull, home);
+            if (hm) {
+                const int leader = __ffs(hm) - 1;
+                int pos = 0;
+                if (lane == leader) pos = atomicAdd(&tail->scount[b], __popc(hm));
+                pos = __shfl_sync(kFull, pos, leader) + __popc(hm & lt);
+                if (home) {
+                    if (pos < capf) __stcs(a.out + fbase + pos, r);
+                    else append_overflow(a, r);
+                }
+            }
+            if (mover) append_mover(a, bt, g, r);
         }
-        int nf, nm;
-        tile_parts(a.cin, t, __ldg(&a.tiles[t].cap), &nf, &nm);
-        float *b = tsm + (size_t)buf * a.buf_floats;
-        advect_tile<LAYOUT, NT>(a, t, b, nf, nf + nm, scount, cur_b, g, s, bt, src, fw);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            a.front_out[t] = *scount;
-            a.lim_out[t] = __ldg(&a.tiles[t].cap) - (nf + nm);
-            *scount = 0;
+        off = (off + nch) % NW;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tail->empty[b]));
+        // refill the buffer of tile j - 1 with tile j + NB - 1, once every
+        // warp has finished tile j - 1 (warp 0 then writes its front count)
+        TileView u;
+        if (more && walk_next(a, sw, u, w0)) {
+            const int jn = j + NB - 1, bn = jn % NB;
+            if (j >= 1) {
+                if (!mbar_wait(smem_u32(&tail->empty[bn]), (uint32_t)((j - 1) / NB) & 1u, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                if (w0 && lane == 0) {
+                    a.front_out[tail->tile[bn]] = min(tail->scount[bn], __ldg(&a.tiles[tail->tile[bn]].capf));
+                    tail->scount[bn] = 0;
+                }
+                fin = j;
+            }
+            if (w0 && lane == 0) tail->tile[bn] = u.t;
+            __syncwarp();
+            stage_share<LAYOUT>(a, u, tsm + (size_t)bn * a.buf_floats, smem_u32(&tail->full[bn]), warp, NW, false);
+            ++staged;
+        } else {
+            more = false;
         }
-        const int tn = t + a.nbuf * G;
-        if (tn < a.ntiles) stage_tile<LAYOUT, NT>(a, tn, b, bar);
     }
-    advect_overflow<LAYOUT, NT>(a);
+    if (ok && w0) {
+        // front counts of the last tiles, as every warp finishes them
+        for (int jj = fin; jj < j; ++jj) {
+            const int bb = jj % NB;
+            if (!mbar_wait(smem_u32(&tail->empty[bb]), (uint32_t)(jj / NB) & 1u, abort_flag, a.err)) {
+                ok = false;
+                break;
+            }
+            if (lane == 0) a.front_out[tail->tile[bb]] = min(tail->scount[bb], __ldg(&a.tiles[tail->tile[bb]].capf));
+        }
+    }
+    if (!ok || *abort_flag) {
+        // Let this warp's copies in flight land before the shared memory is
+        // released; warp 0 then leaves every tile of the CTA empty: their
+        // particles are lost and the error word says so.
+        for (int jj = j; jj < staged; ++jj) mbar_drain(smem_u32(&tail->full[jj % NB]), (uint32_t)(jj / NB) & 1u);
+        if (w0)
+            for (int t = blockIdx.x + lane * (int)gridDim.x; t < a.ntiles; t += 32 * (int)gridDim.x) a.front_out[t] = 0;
+        return;
+    }
+    advect_overflow<LAYOUT>(a, NW);
 }
 
-// Seeds of an interval, straight into the front of their tiles' buckets:
+// Seeds of an interval, straight into the front regions of their tiles:
 // slot tslot[i] holds seed tseed[i] (global id) at its lattice position.
 __global__ void seed_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t nb, const int32_t *__restrict__ tseed,
                                   const int64_t *__restrict__ tslot, int64_t P, float4 *__restrict__ act) {
@@ -426,33 +514,33 @@ __global__ void seed_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t n
     }
 }
 
-// Live record at slot i of a tiled list, or false (tile -1: overflow).
+// Live record at slot i of a tiled list, or false; *tile is the tile whose
+// region holds the slot (-1: the overflow region).
 __device__ __forceinline__ bool live_slot(const TileDev *__restrict__ tiles, const int32_t *__restrict__ unit_tile,
-                                          const TileCounts &c, const int32_t *__restrict__ ocnt, int64_t obase,
-                                          int64_t ocap, int64_t i, int *tile) {
-    if (i < obase) {
+                                          const TileCounts &c, int64_t i, int *tile) {
+    if (i < c.mbase) {
         const int t = unit_tile[i / kUnit];
-        const TileDev &T = tiles[t];
         *tile = t;
-        int nf, nm;
-        tile_parts(c, t, T.cap, &nf, &nm);
-        const int64_t k = i - T.base;
-        return k < nf || k >= T.cap - nm;
+        return i - tiles[t].fbase < min(max(c.front[t], 0), tiles[t].capf);
+    }
+    if (i < c.obase) {
+        const int t = (int)((i - c.mbase) / c.cm);
+        *tile = t;
+        return (i - c.mbase) - (int64_t)t * c.cm < min(max(c.movein[t], 0), c.cm);
     }
     *tile = -1;
-    return i - obase < min(max((int64_t)*ocnt, (int64_t)0), ocap);
+    return i - c.obase < min(max((int64_t)*c.ocnt, (int64_t)0), c.ocap);
 }
 
 __global__ void write_live_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
                                         const TileDev *__restrict__ tiles, const int32_t *__restrict__ unit_tile,
                                         const float4 *__restrict__ act, const TileCounts c,
-                                        const int32_t *__restrict__ ocnt, int64_t obase, int64_t ocap,
                                         float *__restrict__ ends, uint8_t *__restrict__ valid,
                                         int32_t *__restrict__ exit_cycle) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < obase + ocap; i += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.obase + c.ocap; i += stride) {
         int t;
-        if (!live_slot(tiles, unit_tile, c, ocnt, obase, ocap, i, &t)) continue;
+        if (!live_slot(tiles, unit_tile, c, i, &t)) continue;
         const float4 r = act[i];
         const int64_t gid = __float_as_int(r.w);
         const BlockDev &B = blocks[t >= 0 ? tiles[t].b : (nb == 1 ? 0 : find_block(blocks, nb, gid))];
@@ -469,12 +557,11 @@ __global__ void write_live_tiled_kernel(const BlockDev *__restrict__ blocks, int
 __global__ void count_live_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
                                         const TileDev *__restrict__ tiles, const int32_t *__restrict__ unit_tile,
                                         const float4 *__restrict__ act, const TileCounts c,
-                                        const int32_t *__restrict__ ocnt, int64_t obase, int64_t ocap,
                                         unsigned long long *__restrict__ per_block) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < obase + ocap; i += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.obase + c.ocap; i += stride) {
         int t;
-        if (!live_slot(tiles, unit_tile, c, ocnt, obase, ocap, i, &t)) continue;
+        if (!live_slot(tiles, unit_tile, c, i, &t)) continue;
         const int b = t >= 0 ? tiles[t].b : (nb == 1 ? 0 : find_block(blocks, nb, __float_as_int(act[i].w)));
         atomicAdd(per_block + b, 1ull);
     }
@@ -483,12 +570,11 @@ __global__ void count_live_tiled_kernel(const BlockDev *__restrict__ blocks, int
 __global__ void gather_live_tiled_kernel(const BlockDev *__restrict__ blocks, int32_t nb,
                                          const TileDev *__restrict__ tiles, const int32_t *__restrict__ unit_tile,
                                          const float4 *__restrict__ act, const TileCounts c,
-                                         const int32_t *__restrict__ ocnt, int64_t obase, int64_t ocap,
                                          unsigned long long *__restrict__ cursor, float4 *__restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < obase + ocap; i += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.obase + c.ocap; i += stride) {
         int t;
-        if (!live_slot(tiles, unit_tile, c, ocnt, obase, ocap, i, &t)) continue;
+        if (!live_slot(tiles, unit_tile, c, i, &t)) continue;
         float4 r = act[i];
         const int64_t gid = __float_as_int(r.w);
         const int b = t >= 0 ? tiles[t].b : (nb == 1 ? 0 : find_block(blocks, nb, gid));
@@ -501,16 +587,33 @@ __global__ void gather_live_tiled_kernel(const BlockDev *__restrict__ blocks, in
 // The attribute is a ceiling, not an allocation: it is set to the device's
 // opt-in maximum so that contexts with different tile shapes can share the
 // kernel; occupancy and launches use each context's own size.
-template <int LAYOUT, int NT, int MINB>
+template <int LAYOUT, int NW, int MINB>
 cudaError_t tiled_occ(size_t smem, int *n) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(advect_tiled_kernel<LAYOUT, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(advect_tiled_kernel<LAYOUT, NW, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, advect_tiled_kernel<LAYOUT, NT, MINB>, NT, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, advect_tiled_kernel<LAYOUT, NW, MINB>, 32 * NW, smem);
+}
+
+// Each cycle's grid is launched with programmatic stream serialisation, so
+// its launch and CTA set-up overlap the previous cycle's tail.
+template <int LAYOUT, int NW, int MINB>
+cudaError_t tiled_launch_t(const TiledArgs &a, int grid, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32 * NW);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, advect_tiled_kernel<LAYOUT, NW, MINB>, a);
 }
 
 }  // namespace
@@ -525,26 +628,30 @@ size_t tiled_box_bytes(int layout, const int32_t tdim[3], int32_t *pitch, int32_
 }
 
 size_t tiled_smem_bytes(size_t buffer_bytes, int nbuf) {
-    return buffer_bytes * (size_t)nbuf + kMaxBuf * sizeof(uint64_t) + 16;
+    return buffer_bytes * (size_t)nbuf + sizeof(SmemTail) + 16;
 }
 
+// nt = threads per CTA: 128, 256 or 512 (4, 8 or 16 warps, every one both
+// staging and advecting).
+#define BTO_TILED_SHAPES(X) X(LAYOUT_F3, 128, 4, 3) X(LAYOUT_F3, 256, 8, 2) X(LAYOUT_F3, 512, 16, 1) \
+    X(LAYOUT_F4, 128, 4, 3) X(LAYOUT_F4, 256, 8, 2) X(LAYOUT_F4, 512, 16, 1)
+
 cudaError_t tiled_prepare(int layout, int nt, size_t smem, int *ctas_per_sm) {
-    if (layout == LAYOUT_F3 && nt == 128) return tiled_occ<LAYOUT_F3, 128, 4>(smem, ctas_per_sm);
-    if (layout == LAYOUT_F3 && nt == 256) return tiled_occ<LAYOUT_F3, 256, 2>(smem, ctas_per_sm);
-    if (layout == LAYOUT_F4 && nt == 128) return tiled_occ<LAYOUT_F4, 128, 4>(smem, ctas_per_sm);
-    if (layout == LAYOUT_F4 && nt == 256) return tiled_occ<LAYOUT_F4, 256, 2>(smem, ctas_per_sm);
+#define BTO_CASE(L, T, W, M) if (layout == L && nt == T) return tiled_occ<L, W, M>(smem, ctas_per_sm);
+    BTO_TILED_SHAPES(BTO_CASE)
+#undef BTO_CASE
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_advect_tiled(const TiledArgs &a, int layout, int nt, int grid, size_t smem, cudaStream_t s) {
-    if (a.nbuf < 2 || a.nbuf > kMaxBuf) return cudaErrorInvalidValue;
-    if (layout == LAYOUT_F3 && nt == 128) advect_tiled_kernel<LAYOUT_F3, 128, 4><<<grid, 128, smem, s>>>(a);
-    else if (layout == LAYOUT_F3 && nt == 256) advect_tiled_kernel<LAYOUT_F3, 256, 2><<<grid, 256, smem, s>>>(a);
-    else if (layout == LAYOUT_F4 && nt == 128) advect_tiled_kernel<LAYOUT_F4, 128, 4><<<grid, 128, smem, s>>>(a);
-    else if (layout == LAYOUT_F4 && nt == 256) advect_tiled_kernel<LAYOUT_F4, 256, 2><<<grid, 256, smem, s>>>(a);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (a.nbuf < 2 || a.nbuf > kMaxBufs) return cudaErrorInvalidValue;
+#define BTO_CASE(L, T, W, M) if (layout == L && nt == T) return tiled_launch_t<L, W, M>(a, grid, smem, s);
+    BTO_TILED_SHAPES(BTO_CASE)
+#undef BTO_CASE
+    return cudaErrorInvalidValue;
 }
+
+int tiled_max_buffers() { return kMaxBufs; }
 
 cudaError_t launch_seed_tiled(const BlockDev *blocks, int32_t nb, const int32_t *tseed, const int64_t *tslot,
                               int64_t P, float4 *act, int grid, cudaStream_t s) {
@@ -553,28 +660,24 @@ cudaError_t launch_seed_tiled(const BlockDev *blocks, int32_t nb, const int32_t 
 }
 
 cudaError_t launch_write_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
-                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                    const int32_t *ocnt, int64_t obase, int64_t ocap, float *ends,
+                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt, float *ends,
                                     uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s) {
-    write_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt, ocnt, obase, ocap, ends,
-                                                 valid, exit_cycle);
+    write_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt, ends, valid, exit_cycle);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
-                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                    const int32_t *ocnt, int64_t obase, int64_t ocap, int64_t *per_block,
+                                    const int32_t *unit_tile, const float4 *act, TileCounts cnt, int64_t *per_block,
                                     int grid, cudaStream_t s) {
-    count_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt, ocnt, obase, ocap,
+    count_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt,
                                                  reinterpret_cast<unsigned long long *>(per_block));
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_live_tiled(const BlockDev *blocks, int32_t nb, const TileDev *tiles,
-                                     const int32_t *unit_tile, const float4 *act, TileCounts cnt,
-                                     const int32_t *ocnt, int64_t obase, int64_t ocap, int64_t *cursor,
+                                     const int32_t *unit_tile, const float4 *act, TileCounts cnt, int64_t *cursor,
                                      float4 *out, int grid, cudaStream_t s) {
-    gather_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt, ocnt, obase, ocap,
+    gather_live_tiled_kernel<<<grid, 256, 0, s>>>(blocks, nb, tiles, unit_tile, act, cnt,
                                                   reinterpret_cast<unsigned long long *>(cursor), out);
     return cudaGetLastError();
 }
