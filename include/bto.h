@@ -434,7 +434,7 @@ BTO_API void bto_tape_destroy(bto_tape *tape);
  * Seeds are processed in canonical lattice order (not brick order); the
  * outputs are identical to the context calls'. */
 #define BTO_NOALLOC_MAX_SEEDS 65536
-#define BTO_NOALLOC_SCRATCH_BYTES 3432704
+#define BTO_NOALLOC_SCRATCH_BYTES 2375936
 BTO_API bto_status bto_interval_noalloc(const int32_t extent_cells[3], const float origin[3],
                                         const float spacing[3], int32_t seed_stride,
                                         int32_t interval_cycles,

@@ -4,12 +4,12 @@
 //   blocks   [nb] BlockDev          geometry of each block
 //   perm     [P] int32              lattice point of each rank in brick order, per block
 //   gblock   [slots/32] int32       block of each 32-slot unit of the lists
-//   act[2]   [slots] float4         active lists (ping-pong): xi (cell units), id bits
-//   gcnt[2]  [slots/32] int32       live particles per group (ping-pong)
+//   part     [slots] x, y, z, id    particle list, updated in place every cycle:
+//                                   xi (cell units) and block-local id
+//   gcnt     [slots/group] int32    live particles per group (in place)
 //   term     [P] float4             termination record per canonical id: xi, cycle
-// Each block's list region is its seed count rounded up to 128 slots. Cycle c
-// reads act[c%2], gcnt[c%2] and writes act[(c+1)%2], gcnt[(c+1)%2]. No host
-// synchronisation happens on the per-cycle path.
+// Each block's list region is its seed count rounded up to 128 slots. No
+// host synchronisation happens on the per-cycle path.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -40,8 +40,8 @@ struct bto_ctx {
     BlockDev *blocks = nullptr;
     int32_t *perm = nullptr;
     int32_t *gblock = nullptr;
-    float4 *act[2] = {nullptr, nullptr};
-    int32_t *gcnt[2] = {nullptr, nullptr};
+    float *pstate = nullptr;      // [4 * slots]: x, y, z, id arrays of the particle list
+    int32_t *gcnt = nullptr;      // [slots / 32] live particles per group
     float4 *term = nullptr;
     float4 *clip = nullptr;        // [P] first outside point (xi) and stage per canonical id
     int64_t *diag_dst = nullptr;   // bto_copy_active scratch
@@ -193,10 +193,8 @@ void free_ctx(bto_ctx *c) {
     cudaFree(c->blocks);
     cudaFree(c->perm);
     cudaFree(c->gblock);
-    cudaFree(c->act[0]);
-    cudaFree(c->act[1]);
-    cudaFree(c->gcnt[0]);
-    cudaFree(c->gcnt[1]);
+    cudaFree(c->pstate);
+    cudaFree(c->gcnt);
     cudaFree(c->term);
     cudaFree(c->clip);
     cudaFree(c->diag_dst);
@@ -212,6 +210,18 @@ void free_ctx(bto_ctx *c) {
 }
 
 int group_size(const bto_ctx *c) { return 32 * c->ppt; }
+
+// The particle list from slot `first` on (a block's region for per-block
+// launches).
+bto::PartList part_list(const bto_ctx *c, int64_t first = 0) {
+    bto::PartList p;
+    p.x = c->pstate + first;
+    p.y = c->pstate + c->slots + first;
+    p.z = c->pstate + 2 * c->slots + first;
+    p.id = reinterpret_cast<int32_t *>(c->pstate + 3 * c->slots) + first;
+    p.gcnt = c->gcnt + first / group_size(c);
+    return p;
+}
 
 bto_status configure_launch(bto_ctx *c) {
     const bool batched = c->nb > 1;
@@ -258,8 +268,8 @@ bto_status seed(bto_ctx *c, cudaStream_t s) {
         c->cycle = 0;
         return BTO_OK;
     }
-    BTO_CUDA(bto::launch_seed(c->blocks, c->gblock, c->perm, c->slots, group_size(c), c->act[0],
-                              c->gcnt[0], aux_grid(c), s));
+    BTO_CUDA(bto::launch_seed(c->blocks, c->gblock, c->perm, c->slots, group_size(c), part_list(c),
+                              aux_grid(c), s));
     c->cycle = 0;
     return BTO_OK;
 }
@@ -469,10 +479,8 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     e = cudaMalloc(&c->blocks, sizeof(BlockDev) * (size_t)nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)P);
     if (e == cudaSuccess) e = cudaMalloc(&c->gblock, sizeof(int32_t) * units);
-    if (e == cudaSuccess) e = cudaMalloc(&c->act[0], sizeof(float4) * (size_t)slots);
-    if (e == cudaSuccess) e = cudaMalloc(&c->act[1], sizeof(float4) * (size_t)slots);
-    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[0], sizeof(int32_t) * units);
-    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt[1], sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = cudaMalloc(&c->pstate, 4 * sizeof(float) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt, sizeof(int32_t) * units);
     if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
     if (e == cudaSuccess) e = cudaMalloc(&c->clip, sizeof(float4) * (size_t)P);
     if (e == cudaSuccess) e = cudaMalloc(&c->derr, sizeof(int32_t));
@@ -485,8 +493,7 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
         e = cudaMemcpy(c->gblock, gblock.data(), sizeof(int32_t) * units, cudaMemcpyHostToDevice);
     // term records start as "not terminated" (w = -1: all bits set)
     if (e == cudaSuccess) e = cudaMemset(c->term, 0xff, sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMemset(c->gcnt[0], 0, sizeof(int32_t) * units);
-    if (e == cudaSuccess) e = cudaMemset(c->gcnt[1], 0, sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = cudaMemset(c->gcnt, 0, sizeof(int32_t) * units);
     if (e != cudaSuccess) { (void)cudaGetLastError(); free_ctx(c); return cuda_status(e); }
 
     bto_status st = configure_launch(c);
@@ -523,10 +530,7 @@ bto_status advect_ingest(bto_ctx *c, const void *field, const void *const *field
         a.cycle = cyc;
         a.field = c->f4buf[k];
         a.fields = nullptr;
-        a.in = c->act[cyc & 1] + B.slot_base;
-        a.out = c->act[(cyc + 1) & 1] + B.slot_base;
-        a.gcnt_in = c->gcnt[cyc & 1] + B.slot_base / G;
-        a.gcnt_out = c->gcnt[(cyc + 1) & 1] + B.slot_base / G;
+        a.p = part_list(c, B.slot_base);
         a.ngroups = region / G;
         a.term = c->term;
         a.clip = c->clip;
@@ -606,10 +610,7 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     a.cycle = cyc;
     a.field = field;
     a.fields = fields;
-    a.in = c->act[cyc & 1];
-    a.out = c->act[(cyc + 1) & 1];
-    a.gcnt_in = c->gcnt[cyc & 1];
-    a.gcnt_out = c->gcnt[(cyc + 1) & 1];
+    a.p = part_list(c);
     a.ngroups = c->slots / group_size(c);
     a.term = c->term;
     a.clip = c->clip;
@@ -772,7 +773,7 @@ bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends, uint
                                               tile_counts(ctx, L), d_ends, d_valid, d_exit_cycle,
                                               tiled_aux_grid(ctx), s));
     else
-        BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, ctx->act[L & 1], ctx->gcnt[L & 1],
+        BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, part_list(ctx),
                                         ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
                                         grid, s));
     BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
@@ -967,7 +968,7 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
     const int64_t ng = ctx->slots / G;
     std::vector<int32_t> cnt((size_t)ng);
     std::vector<int64_t> dst((size_t)ng);
-    BTO_CUDA(cudaMemcpyAsync(cnt.data(), ctx->gcnt[cyc & 1], sizeof(int32_t) * (size_t)ng,
+    BTO_CUDA(cudaMemcpyAsync(cnt.data(), ctx->gcnt, sizeof(int32_t) * (size_t)ng,
                              cudaMemcpyDeviceToHost, s));
     BTO_CUDA(cudaStreamSynchronize(s));
     for (int32_t b = 0; b < ctx->nb; ++b) {
@@ -984,7 +985,7 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
     if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)(ctx->slots / 32)));
     BTO_CUDA(cudaMemcpyAsync(ctx->diag_dst, dst.data(), sizeof(int64_t) * (size_t)ng,
                              cudaMemcpyHostToDevice, s));
-    BTO_CUDA(bto::launch_gather_live(ctx->act[cyc & 1], ctx->gcnt[cyc & 1], ctx->diag_dst, ctx->slots,
+    BTO_CUDA(bto::launch_gather_live(part_list(ctx), ctx->diag_dst, ctx->slots,
                                      G, reinterpret_cast<float4 *>(d_out), aux_grid(ctx), s));
     BTO_CUDA(cudaStreamSynchronize(s));
     return BTO_OK;

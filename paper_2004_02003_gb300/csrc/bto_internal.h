@@ -30,9 +30,19 @@ struct BlockDev {
 constexpr int kRegionAlign = 128;
 constexpr int kUnit = 32;
 
+// Particle state of the untiled path, updated in place every cycle. Slot
+// i holds the position in cell units (x[i], y[i], z[i]) and the block-local
+// canonical id id[i]; the list is cut into groups of G = 32 * ppt slots,
+// and group g holds its gcnt[g] live particles in its first slots, in
+// brick order of their seeds. Positions are read and written every cycle;
+// ids move only when a group loses a particle.
+struct PartList {
+    float *x, *y, *z;
+    int32_t *id;
+    int32_t *gcnt;
+};
+
 // Arguments of one advection cycle (kernel K3: RK4 + termination + compaction).
-// The active list is cut into groups of G = 32 * ppt slots; group g holds
-// gcnt[g] live particles in its first slots, in brick order of their seeds.
 struct AdvectArgs {
     const BlockDev *blocks;      // [nb] device
     const int32_t *gblock;       // [slots / 32] block of each 32-slot unit
@@ -40,10 +50,7 @@ struct AdvectArgs {
     int32_t cycle;               // cycle index within the interval
     const void *field;           // single field pointer (nb == 1 calls), or NULL
     const void *const *fields;   // device array [nb] used when field == NULL
-    const float4 *in;            // active list at cycle start (xi, id bits)
-    float4 *out;                 // active list after the cycle
-    const int32_t *gcnt_in;      // [ngroups] live particles per group at cycle start
-    int32_t *gcnt_out;           // [ngroups] survivors per group
+    PartList p;                  // particle state (groups from 0 to ngroups - 1)
     int64_t ngroups;
     float4 *term;                // [P] termination record per canonical id
     float4 *clip;                // [P] first outside point (xi) and its RK4 stage, or NULL
@@ -157,13 +164,12 @@ cudaError_t launch_count_live_tiled(const BlockDev *blocks, int32_t nb, const Ti
                                     int64_t *per_block, int grid, cudaStream_t s);
 
 cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,
-                        int64_t slots, int group, float4 *act, int32_t *gcnt, int grid,
-                        cudaStream_t s);
-cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, const float4 *act,
-                              const int32_t *gcnt, int64_t slots, int group, float *ends,
-                              uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s);
-cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
-                               int64_t slots, int group, float4 *out, int grid, cudaStream_t s);
+                        int64_t slots, int group, PartList p, int grid, cudaStream_t s);
+cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, PartList p, int64_t slots,
+                              int group, float *ends, uint8_t *valid, int32_t *exit_cycle, int grid,
+                              cudaStream_t s);
+cudaError_t launch_gather_live(PartList p, const int64_t *dst, int64_t slots, int group, float4 *out,
+                               int grid, cudaStream_t s);
 cudaError_t launch_ingest(const void *field, const void *const *fields, int b, int64_t nodes, float4 *out,
                           int grid, cudaStream_t s);
 cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,

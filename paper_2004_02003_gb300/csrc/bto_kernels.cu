@@ -45,13 +45,15 @@ __device__ __forceinline__ int find_block(const BlockDev *__restrict__ blocks, i
 }
 
 // ---------------------------------------------------------------------------
-// K3: advection cycle. The active list is cut into groups of G = 32*PPT
+// K3: advection cycle. The particle list is cut into groups of G = 32*PPT
 // slots; one warp owns a group for the cycle: it advects the group's live
-// particles (PPT rounds of 32) and writes the survivors, in order, to the
-// front of the same group in the output list. Warps take groups g, g + W,
-// g + 2W, ... (W = warps in the grid), so the groups in flight at any time
-// are neighbours in brick order. There is no barrier and no atomic: a
-// terminated particle only leaves the group's live prefix.
+// particles (PPT rounds of 32) and writes them back in place. When none of
+// them terminated, only the positions are rewritten, in their slots; when
+// some did, the survivors (positions and ids) are compacted, in order, to
+// the front of the group. Warps take groups g, g + W, g + 2W, ... (W =
+// warps in the grid), so the groups in flight at any time are neighbours
+// in brick order. There is no barrier and no atomic: a terminated particle
+// only leaves the group's live prefix.
 // ---------------------------------------------------------------------------
 template <int LAYOUT, int NT, int PPT, bool BATCHED, int MINB>
 __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
@@ -70,14 +72,12 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
     float3 s = make_float3(0.f, 0.f, 0.f);
     const void *field = nullptr;
     int64_t idbase = 0;
+    const PartList P = a.p;
 
     for (int64_t grp = (((int64_t)blockIdx.x * NT) + threadIdx.x) >> 5; grp < a.ngroups;
          grp += nwarps) {
-        const int cnt = __ldcg(a.gcnt_in + grp);
-        if (cnt == 0) {
-            if (lane == 0) a.gcnt_out[grp] = 0;
-            continue;
-        }
+        const int cnt = __ldcg(P.gcnt + grp);
+        if (cnt == 0) continue;
         const int b = BATCHED ? __ldg(a.gblock + grp * PPT) : 0;
         if (b != cur_b) {
             cur_b = b;
@@ -88,35 +88,66 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
             idbase = B.base;
         }
         const int64_t s0 = grp * G;
-        float4 r[PPT];
+        float3 r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int i = k * 32 + lane;
-            r[k] = i < cnt ? __ldcs(a.in + s0 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            r[k] = make_float3(0.f, 0.f, 0.f);
+            if (i < cnt) r[k] = make_float3(__ldcs(P.x + s0 + i), __ldcs(P.y + s0 + i), __ldcs(P.z + s0 + i));
         }
-        int kept = 0;
+        unsigned surv = 0;   // bit k: the lane's particle of round k survived
+        bool term = false;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int i = k * 32 + lane;
-            bool surv = false;
             if (i < cnt) {
-                float3 x = make_float3(r[k].x, r[k].y, r[k].z), q;
+                float3 x = r[k], q;
                 const int failed = rk4_step<LAYOUT>(x, field, g, s, q);
-                surv = failed == 0;
-                if (surv) {
-                    r[k].x = x.x; r[k].y = x.y; r[k].z = x.z;
+                if (failed == 0) {
+                    r[k] = x;
+                    surv |= 1u << k;
                 } else {
-                    const int64_t gid = idbase + __float_as_int(r[k].w);
+                    term = true;
+                    const int64_t gid = idbase + __ldcs(P.id + s0 + i);
                     __stcs(a.term + gid, make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
                     // first outside point and its stage; clipped at the interval end
                     if (a.clip) __stcs(a.clip + gid, make_float4(q.x, q.y, q.z, __int_as_float(failed)));
                 }
             }
-            const unsigned m = __ballot_sync(kFull, surv);
-            if (surv) __stcs(a.out + s0 + kept + __popc(m & lt), r[k]);
-            kept += __popc(m);
         }
-        if (lane == 0) a.gcnt_out[grp] = kept;
+        if (!__any_sync(kFull, term)) {
+            // nobody left: positions back in their slots, ids untouched
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int64_t i = s0 + k * 32 + lane;
+                if (k * 32 + lane < cnt) {
+                    __stcs(P.x + i, r[k].x);
+                    __stcs(P.y + i, r[k].y);
+                    __stcs(P.z + i, r[k].z);
+                }
+            }
+        } else {
+            // survivors to the front of the group; every id of the group is
+            // read before the first write
+            int id[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) id[k] = (surv >> k) & 1u ? __ldcs(P.id + s0 + k * 32 + lane) : 0;
+            int kept = 0;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const bool sv = (surv >> k) & 1u;
+                const unsigned m = __ballot_sync(kFull, sv);
+                if (sv) {
+                    const int64_t j = s0 + kept + __popc(m & lt);
+                    __stcs(P.x + j, r[k].x);
+                    __stcs(P.y + j, r[k].y);
+                    __stcs(P.z + j, r[k].z);
+                    __stcs(P.id + j, id[k]);
+                }
+                kept += __popc(m);
+            }
+            if (lane == 0) P.gcnt[grp] = kept;
+        }
     }
 }
 
@@ -126,41 +157,40 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
 // integers j*s in cell units. Also sets every group's live count.
 // ---------------------------------------------------------------------------
 __global__ void seed_kernel(const BlockDev *__restrict__ blocks, const int32_t *__restrict__ gblock,
-                            const int32_t *__restrict__ perm, int64_t slots, int group,
-                            float4 *__restrict__ act, int32_t *__restrict__ gcnt) {
+                            const int32_t *__restrict__ perm, int64_t slots, int group, PartList P) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
         const BlockDev &B = blocks[gblock[i / kUnit]];
         const int64_t m = i - B.slot_base;
         if (i % group == 0) {
             const int64_t left = B.nseeds - m;
-            gcnt[i / group] = (int32_t)(left < 0 ? 0 : (left > group ? group : left));
+            P.gcnt[i / group] = (int32_t)(left < 0 ? 0 : (left > group ? group : left));
         }
         if (m >= B.nseeds) continue;
         const int32_t p = perm[B.base + m];
         const int32_t jx = p % B.S[0];
         const int32_t jy = (p / B.S[0]) % B.S[1];
         const int32_t jz = p / (B.S[0] * B.S[1]);
-        act[i] = make_float4((float)(jx * B.stride), (float)(jy * B.stride), (float)(jz * B.stride),
-                             __int_as_float(p));
+        P.x[i] = (float)(jx * B.stride);
+        P.y[i] = (float)(jy * B.stride);
+        P.z[i] = (float)(jz * B.stride);
+        P.id[i] = p;
     }
 }
 
 // K4a: particles alive at the end of the interval.
 __global__ void write_live_kernel(const BlockDev *__restrict__ blocks,
-                                  const int32_t *__restrict__ gblock,
-                                  const float4 *__restrict__ act, const int32_t *__restrict__ gcnt,
+                                  const int32_t *__restrict__ gblock, const PartList P,
                                   int64_t slots, int group, float *__restrict__ ends,
                                   uint8_t *__restrict__ valid, int32_t *__restrict__ exit_cycle) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
-        if (i % group >= gcnt[i / group]) continue;
+        if (i % group >= P.gcnt[i / group]) continue;
         const BlockDev &B = blocks[gblock[i / kUnit]];
-        const float4 r = act[i];
-        const int64_t gid = B.base + __float_as_int(r.w);
-        ends[3 * gid + 0] = fmaf(r.x, B.h[0], B.origin[0]);
-        ends[3 * gid + 1] = fmaf(r.y, B.h[1], B.origin[1]);
-        ends[3 * gid + 2] = fmaf(r.z, B.h[2], B.origin[2]);
+        const int64_t gid = B.base + P.id[i];
+        ends[3 * gid + 0] = fmaf(P.x[i], B.h[0], B.origin[0]);
+        ends[3 * gid + 1] = fmaf(P.y[i], B.h[1], B.origin[1]);
+        ends[3 * gid + 2] = fmaf(P.z[i], B.h[2], B.origin[2]);
         if (valid) valid[gid] = 1;
         if (exit_cycle) exit_cycle[gid] = -1;
     }
@@ -222,15 +252,15 @@ __global__ void write_term_kernel(const BlockDev *__restrict__ blocks, int32_t n
     }
 }
 
-// Diagnostics: live particles of each group copied to dst[g] + k.
-__global__ void gather_live_kernel(const float4 *__restrict__ act, const int32_t *__restrict__ gcnt,
-                                   const int64_t *__restrict__ dst, int64_t slots, int group,
-                                   float4 *__restrict__ out) {
+// Diagnostics: live particles of each group copied to dst[g] + k as
+// (xi, block-local id bits).
+__global__ void gather_live_kernel(const PartList P, const int64_t *__restrict__ dst, int64_t slots,
+                                   int group, float4 *__restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
         const int64_t g = i / group;
         const int k = (int)(i % group);
-        if (k < gcnt[g]) out[dst[g] + k] = act[i];
+        if (k < P.gcnt[g]) out[dst[g] + k] = make_float4(P.x[i], P.y[i], P.z[i], __int_as_float(P.id[i]));
     }
 }
 
@@ -323,23 +353,21 @@ cudaError_t advect_occupancy(int layout, int nt, int ppt, bool cap, bool batched
 }
 
 cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int32_t *perm,
-                        int64_t slots, int group, float4 *act, int32_t *gcnt, int grid,
-                        cudaStream_t s) {
-    seed_kernel<<<grid, 256, 0, s>>>(blocks, gblock, perm, slots, group, act, gcnt);
+                        int64_t slots, int group, PartList p, int grid, cudaStream_t s) {
+    seed_kernel<<<grid, 256, 0, s>>>(blocks, gblock, perm, slots, group, p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, const float4 *act,
-                              const int32_t *gcnt, int64_t slots, int group, float *ends,
-                              uint8_t *valid, int32_t *exit_cycle, int grid, cudaStream_t s) {
-    write_live_kernel<<<grid, 256, 0, s>>>(blocks, gblock, act, gcnt, slots, group, ends, valid,
-                                           exit_cycle);
+cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, PartList p, int64_t slots,
+                              int group, float *ends, uint8_t *valid, int32_t *exit_cycle, int grid,
+                              cudaStream_t s) {
+    write_live_kernel<<<grid, 256, 0, s>>>(blocks, gblock, p, slots, group, ends, valid, exit_cycle);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_live(const float4 *act, const int32_t *gcnt, const int64_t *dst,
-                               int64_t slots, int group, float4 *out, int grid, cudaStream_t s) {
-    gather_live_kernel<<<grid, 256, 0, s>>>(act, gcnt, dst, slots, group, out);
+cudaError_t launch_gather_live(PartList p, const int64_t *dst, int64_t slots, int group, float4 *out,
+                               int grid, cudaStream_t s) {
+    gather_live_kernel<<<grid, 256, 0, s>>>(p, dst, slots, group, out);
     return cudaGetLastError();
 }
 

@@ -32,14 +32,14 @@ constexpr int64_t kMaxSeeds = BTO_NOALLOC_MAX_SEEDS;
 constexpr int64_t kMaxSlots = (kMaxSeeds + bto::kRegionAlign - 1) / bto::kRegionAlign * bto::kRegionAlign;
 constexpr int64_t kMaxUnits = kMaxSlots / bto::kUnit;
 
-// Byte offsets of the parts of the scratch array (each 256-byte aligned).
+// Byte offsets of the parts of the scratch array (each 256-byte aligned):
+// the particle list (x, y, z and id arrays), the termination records, the
+// group counts, the seed order, the 32-slot-unit block map and the block.
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
-constexpr size_t kOffAct0 = 0;
-constexpr size_t kOffAct1 = kOffAct0 + align256(sizeof(float4) * kMaxSlots);
-constexpr size_t kOffTerm = kOffAct1 + align256(sizeof(float4) * kMaxSlots);
-constexpr size_t kOffGcnt0 = kOffTerm + align256(sizeof(float4) * kMaxSeeds);
-constexpr size_t kOffGcnt1 = kOffGcnt0 + align256(sizeof(int32_t) * kMaxUnits);
-constexpr size_t kOffPerm = kOffGcnt1 + align256(sizeof(int32_t) * kMaxUnits);
+constexpr size_t kOffPart = 0;
+constexpr size_t kOffTerm = kOffPart + align256(4 * sizeof(float) * kMaxSlots);
+constexpr size_t kOffGcnt = kOffTerm + align256(sizeof(float4) * kMaxSeeds);
+constexpr size_t kOffPerm = kOffGcnt + align256(sizeof(int32_t) * kMaxUnits);
 constexpr size_t kOffGblock = kOffPerm + align256(sizeof(int32_t) * kMaxSeeds);
 constexpr size_t kOffBlock = kOffGblock + align256(sizeof(int32_t) * kMaxUnits);
 constexpr size_t kScratchBytes = kOffBlock + align256(sizeof(BlockDev));
@@ -131,17 +131,19 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
     unsigned char *base = nullptr;
     const bto_status st = scratch_address(&base);
     if (st != BTO_OK) return st;
-    float4 *act[2] = {reinterpret_cast<float4 *>(base + kOffAct0),
-                      reinterpret_cast<float4 *>(base + kOffAct1)};
     float4 *term = reinterpret_cast<float4 *>(base + kOffTerm);
-    int32_t *gcnt[2] = {reinterpret_cast<int32_t *>(base + kOffGcnt0),
-                        reinterpret_cast<int32_t *>(base + kOffGcnt1)};
     int32_t *perm = reinterpret_cast<int32_t *>(base + kOffPerm);
     int32_t *gblock = reinterpret_cast<int32_t *>(base + kOffGblock);
     BlockDev *blk = reinterpret_cast<BlockDev *>(base + kOffBlock);
 
     const int64_t slots = (B.nseeds + bto::kRegionAlign - 1) / bto::kRegionAlign * bto::kRegionAlign;
     const int nt = 128, ppt = 2, group = 32 * ppt;
+    bto::PartList part;
+    part.x = reinterpret_cast<float *>(base + kOffPart);
+    part.y = part.x + slots;
+    part.z = part.y + slots;
+    part.id = reinterpret_cast<int32_t *>(part.z + slots);
+    part.gcnt = reinterpret_cast<int32_t *>(base + kOffGcnt);
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -158,7 +160,7 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
 
     noalloc_init_kernel<<<aux, 256, 0, s>>>(B, slots, blk, perm, gblock, term);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = bto::launch_seed(blk, gblock, perm, slots, group, act[0], gcnt[0], aux, s);
+    if (e == cudaSuccess) e = bto::launch_seed(blk, gblock, perm, slots, group, part, aux, s);
     for (int32_t c = 0; c < interval_cycles && e == cudaSuccess; ++c) {
         bto::AdvectArgs a{};
         a.blocks = blk;
@@ -167,19 +169,14 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
         a.cycle = c;
         a.field = nullptr;
         a.fields = d_field_table + c;
-        a.in = act[c & 1];
-        a.out = act[(c + 1) & 1];
-        a.gcnt_in = gcnt[c & 1];
-        a.gcnt_out = gcnt[(c + 1) & 1];
+        a.p = part;
         a.ngroups = ngroups;
         a.term = term;
         a.dt = dt;
         e = bto::launch_advect(a, bto::LAYOUT_F3, nt, ppt, false, grid, 0, s);
     }
-    const int L = interval_cycles;
     if (e == cudaSuccess)
-        e = bto::launch_write_live(blk, gblock, act[L & 1], gcnt[L & 1], slots, group, d_ends, d_valid,
-                                   d_exit_cycle, aux, s);
+        e = bto::launch_write_live(blk, gblock, part, slots, group, d_ends, d_valid, d_exit_cycle, aux, s);
     if (e == cudaSuccess)
         e = bto::launch_write_term(blk, 1, B.nseeds, term, d_seeds, d_ends, d_valid, d_exit_cycle, aux, s);
     if (e != cudaSuccess) {
