@@ -45,6 +45,7 @@
 #ifndef BTO_H
 #define BTO_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -69,7 +70,8 @@ typedef enum {
     BTO_ERR_CUDA = 3,        /* a CUDA call or launch failed */
     BTO_ERR_OOM = 4,         /* device or host allocation failed */
     BTO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    BTO_ERR_UNSUPPORTED = 6  /* valid request this build does not handle */
+    BTO_ERR_UNSUPPORTED = 6, /* valid request this build does not handle */
+    BTO_ERR_BOUNDS = 7       /* a bounds check failed (bounds-checked builds only) */
 } bto_status;
 
 /* Field layouts accepted by bto_advect_cycle.
@@ -413,14 +415,19 @@ BTO_API void bto_tape_destroy(bto_tape *tape);
  * and calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * The particle state lives in a fixed array of BTO_NOALLOC_SCRATCH_BYTES in
- * the library's device image. Every device that loads the library holds that
- * array until the process exits. All calls on a device share it, and it keeps
- * the last call's contents (each call rewrites what it reads first), so calls
- * whose GPU work overlaps (different streams, or several host threads) race
- * with each other and give wrong results: order them on one stream.
- * The first call on each device, made with that device current, looks up the
- * array's device address (cudaGetSymbolAddress) and keeps it; make that first
- * call before any stream capture.
+ * the library's device image. The CUDA runtime loads that image on a device
+ * lazily (its default module loading): the first call on each device, made
+ * with that device current, loads it, which reserves the array's
+ * BTO_NOALLOC_SCRATCH_BYTES of device memory there, looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it. That first call is
+ * therefore itself a device allocation by the runtime: make it once at
+ * start-up, before handing device memory to a pool allocator and before any
+ * stream capture; later calls on that device allocate nothing. The array
+ * stays reserved until the process exits. All calls on a device share it,
+ * and it keeps the last call's contents (each call rewrites what it reads
+ * first), so calls whose GPU work overlaps (different streams, or several
+ * host threads) race with each other and give wrong results: order them on
+ * one stream.
  *
  *   extent_cells, origin, spacing, seed_stride, interval_cycles
  *                  as in bto_create; at most BTO_NOALLOC_MAX_SEEDS seeds
@@ -441,6 +448,46 @@ BTO_API bto_status bto_interval_noalloc(const int32_t extent_cells[3], const flo
                                         const void *const *d_field_table, float dt,
                                         float *d_seeds, float *d_ends, uint8_t *d_valid,
                                         int32_t *d_exit_cycle, bto_stream stream);
+
+/* ---- Device allocator hook (no counterpart in the paper) ----------------
+ *
+ * For callers whose own pool allocator owns the device memory: once a hook is
+ * installed, every device allocation the library makes for a context or a
+ * tape (bto_create, bto_batch_create, bto_set_tiling, bto_set_ingest,
+ * bto_copy_active, bto_tape_create) calls alloc(bytes, user) instead of
+ * cudaMalloc, and frees with free_fn(ptr, user) instead of cudaFree.
+ *   alloc     returns a device pointer to at least `bytes` bytes, 256-byte
+ *             aligned, on the current device; or NULL: the calling function
+ *             then frees what it had allocated through free_fn and returns
+ *             BTO_ERR_OOM. A misaligned pointer is freed again and the call
+ *             returns BTO_ERR_CUDA.
+ *   free_fn   releases a pointer alloc returned.
+ * Both NULL restores cudaMalloc / cudaFree; one NULL: BTO_ERR_INVALID_ARG.
+ * Process-wide; a context or tape keeps the hook that was installed when it
+ * was created and frees through it, so the hook's memory must outlive it.
+ * Allocations by the CUDA runtime itself (module loading, streams, graphs)
+ * do not go through the hook. */
+typedef void *(*bto_alloc_fn)(size_t bytes, void *user);
+typedef void (*bto_free_fn)(void *ptr, void *user);
+BTO_API bto_status bto_set_device_allocator(bto_alloc_fn alloc, bto_free_fn free_fn, void *user);
+
+/* ---- Bounds-checked builds (no counterpart in the paper) ----------------
+ *
+ * Compiled with BTO_CHECK_BOUNDS defined (build.build(check_bounds=True)),
+ * the kernels test every field-node index of a global gather, every group
+ * count and particle id of the particle list, every destination tile of the
+ * tiled path and every lattice index of the post hoc kernels before using
+ * it. A failed test skips the access (a node or lattice index is replaced by
+ * 0, a write is dropped), adds one to a failure counter and, for the kernels
+ * of a context, sets the context's error word, which bto_last_error returns
+ * as BTO_ERR_BOUNDS. No check traps. Product builds compile the tests out.
+ *
+ * bto_check_bounds_build: 1 for a bounds-checked build, 0 otherwise.
+ * bto_bounds_failures:    failed checks since load (or the last reset) in
+ *                         *count (0 in product builds); reset != 0 clears
+ *                         the counters. Synchronous: waits for the device. */
+BTO_API int32_t bto_check_bounds_build(void);
+BTO_API bto_status bto_bounds_failures(uint64_t *count, int32_t reset);
 
 /* Static string for a status code. */
 BTO_API const char *bto_status_string(bto_status status);

@@ -26,12 +26,21 @@ BTO_ERR_CUDA = 3
 BTO_ERR_OOM = 4
 BTO_ERR_TIMEOUT = 5
 BTO_ERR_UNSUPPORTED = 6
+BTO_ERR_BOUNDS = 7
 BTO_FIELD_F3_AOS = 0
 BTO_FIELD_F4_AOS = 1
 BTO_STITCH_TRILINEAR = 0
 BTO_STITCH_BARYCENTRIC = 1
 
 _lib = None
+
+# C types of the device allocator hook (include/bto.h)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+# Every allocator callback pair ever installed, kept alive for the life of
+# the process: a context or tape keeps the hook it was created with and may
+# free through it after another hook (or none) has been installed.
+_allocator_refs = []
 
 
 class BtoError(RuntimeError):
@@ -43,6 +52,7 @@ class BtoError(RuntimeError):
 def _declare(lib):
     c_i32p = ctypes.POINTER(ctypes.c_int32)
     c_i64p = ctypes.POINTER(ctypes.c_int64)
+    c_u64p = ctypes.POINTER(ctypes.c_uint64)
     c_fp = ctypes.POINTER(ctypes.c_float)
     vp = ctypes.c_void_p
     sig = {
@@ -71,6 +81,9 @@ def _declare(lib):
         "bto_interval_noalloc": ([c_i32p, c_fp, c_fp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_float,
                                   vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_destroy": ([vp], None),
+        "bto_set_device_allocator": ([ALLOC_FN, FREE_FN, vp], ctypes.c_int),
+        "bto_check_bounds_build": ([], ctypes.c_int32),
+        "bto_bounds_failures": ([c_u64p, ctypes.c_int32], ctypes.c_int),
         "bto_fill_lattice": ([c_i32p, vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_stitch_pathlines": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp],
                                  ctypes.c_int),
@@ -92,12 +105,15 @@ def _declare(lib):
 
 
 def load():
-    """Load libbto.so (raises BtoError if it has not been built)."""
+    """Load libbto.so (raises BtoError if it has not been built). The
+    environment variable BTO_LIBRARY names another build of the same library
+    to load instead (the bounds-checked build, for instance)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise BtoError(BTO_ERR_UNSUPPORTED, f"libbto not built ({LIB_PATH} missing)")
-        lib = ctypes.CDLL(LIB_PATH)
+        path = os.environ.get("BTO_LIBRARY") or LIB_PATH
+        if not os.path.exists(path):
+            raise BtoError(BTO_ERR_UNSUPPORTED, f"libbto not built ({path} missing)")
+        lib = ctypes.CDLL(path)
         _declare(lib)
         _lib = lib
     return _lib
@@ -277,6 +293,29 @@ def bto_interval_noalloc(extent_cells, origin, spacing, seed_stride: int, interv
                                        _addr(d_field_table), float(dt), _addr(d_seeds), _addr(d_ends),
                                        _addr(d_valid), _addr(d_exit_cycle), _stream(stream)),
            "bto_interval_noalloc")
+
+
+def bto_set_device_allocator(alloc=None, free=None) -> None:
+    """Install Python callables as the library's device allocator:
+    alloc(nbytes) -> device address (int) or 0, free(address) -> None.
+    Both None restores cudaMalloc / cudaFree."""
+    if alloc is None and free is None:
+        _check(load().bto_set_device_allocator(ALLOC_FN(), FREE_FN(), None), "bto_set_device_allocator")
+        return
+    a = ALLOC_FN(lambda nbytes, user: int(alloc(int(nbytes))) or None)
+    f = FREE_FN(lambda ptr, user: free(int(ptr)))
+    _allocator_refs.append((a, f))
+    _check(load().bto_set_device_allocator(a, f, None), "bto_set_device_allocator")
+
+
+def bto_check_bounds_build() -> bool:
+    return bool(load().bto_check_bounds_build())
+
+
+def bto_bounds_failures(reset: bool = False) -> int:
+    v = ctypes.c_uint64(0)
+    _check(load().bto_bounds_failures(ctypes.byref(v), int(bool(reset))), "bto_bounds_failures")
+    return int(v.value)
 
 
 def bto_fill_lattice(lattice, d_ends, d_valid, d_out, d_status=None, stream=None) -> None:

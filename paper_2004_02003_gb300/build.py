@@ -2,7 +2,10 @@
 
 ``python -m paper_2004_02003_gb300.build`` compiles every ``csrc/*.cu``
 translation unit in parallel with nvcc for sm_103a and links
-``_build/libbto.so``. Nothing is installed outside the package directory.
+``_build/libbto.so``. ``build(check_bounds=True)`` (``--check-bounds``)
+links the bounds-checked build, ``_build/check/libbto.so``, with
+BTO_CHECK_BOUNDS defined. Nothing is installed outside the package
+directory.
 """
 from __future__ import annotations
 
@@ -18,6 +21,8 @@ BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libbto.so")
+CHECK_BUILD = os.path.join(BUILD, "check")
+CHECK_LIB = os.path.join(CHECK_BUILD, "libbto.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
@@ -40,24 +45,26 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, check_bounds: bool = False) -> str:
+    out_dir, lib = (CHECK_BUILD, CHECK_LIB) if check_bounds else (BUILD, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *(["-DBTO_CHECK_BOUNDS"] if check_bounds else []), "-I", INCLUDE,
+               "-c", src, "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         if verbose:
@@ -73,14 +80,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             print(text, end="")
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="-v" in sys.argv,
+                check_bounds="--check-bounds" in sys.argv))

@@ -37,6 +37,7 @@
 using bto::BlockDev;
 
 struct bto_tape {
+    bto::DevAlloc mem;           // device allocator captured at creation
     int device = 0;
     int sm_count = 0;
     BlockDev B{};
@@ -361,11 +362,11 @@ int grid_of(const bto_tape *t) {
 
 void free_tape(bto_tape *t) {
     if (!t) return;
-    cudaFree(t->ckpt);
-    cudaFree(t->seg);
-    cudaFree(t->lam);
-    cudaFree(t->d_block);
-    cudaFree(t->exitc);
+    t->mem.put(t->ckpt);
+    t->mem.put(t->seg);
+    t->mem.put(t->lam);
+    t->mem.put(t->d_block);
+    t->mem.put(t->exitc);
     delete t;
 }
 
@@ -406,6 +407,7 @@ bto_status bto_tape_create(const int32_t extent_cells[3], const float origin[3],
     B.nseeds = num_particles;
     bto_tape *t = new (std::nothrow) bto_tape();
     if (!t) return BTO_ERR_OOM;
+    t->mem = bto::current_allocator();
     t->B = B;
     t->P = num_particles;
     t->L = cycles;
@@ -414,11 +416,11 @@ bto_status bto_tape_create(const int32_t extent_cells[3], const float origin[3],
     cudaError_t e = cudaGetDevice(&t->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device);
     const size_t P = (size_t)num_particles;
-    if (e == cudaSuccess) e = cudaMalloc(&t->ckpt, sizeof(float4) * P * (size_t)t->nck);
-    if (e == cudaSuccess) e = cudaMalloc(&t->seg, sizeof(float4) * 3 * P * (size_t)t->K);
-    if (e == cudaSuccess) e = cudaMalloc(&t->lam, sizeof(float4) * 3 * P);
-    if (e == cudaSuccess) e = cudaMalloc(&t->d_block, sizeof(BlockDev));
-    if (e == cudaSuccess) e = cudaMalloc(&t->exitc, sizeof(int32_t) * P);
+    if (e == cudaSuccess) e = t->mem.get(&t->ckpt, sizeof(float4) * P * (size_t)t->nck);
+    if (e == cudaSuccess) e = t->mem.get(&t->seg, sizeof(float4) * 3 * P * (size_t)t->K);
+    if (e == cudaSuccess) e = t->mem.get(&t->lam, sizeof(float4) * 3 * P);
+    if (e == cudaSuccess) e = t->mem.get(&t->d_block, sizeof(BlockDev));
+    if (e == cudaSuccess) e = t->mem.get(&t->exitc, sizeof(int32_t) * P);
     if (e == cudaSuccess) e = cudaMemcpy(t->d_block, &t->B, sizeof(BlockDev), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -4,8 +4,9 @@
 //   blocks   [nb] BlockDev          geometry of each block
 //   perm     [P] int32              lattice point of each rank in brick order, per block
 //   gblock   [slots/32] int32       block of each 32-slot unit of the lists
-//   part     [slots] x, y, z, id    particle list, updated in place every cycle:
-//                                   xi (cell units) and block-local id
+//   pstate   [4 slots] float        particle list, updated in place every cycle:
+//                                   units of 32 slots holding 32 x, 32 y, 32 z
+//                                   (cell units), 32 block-local ids
 //   gcnt     [slots/group] int32    live particles per group (in place)
 //   term     [P] float4             termination record per canonical id: xi, cycle
 // Each block's list region is its seed count rounded up to 128 slots. No
@@ -14,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -25,6 +27,7 @@
 using bto::BlockDev;
 
 struct bto_ctx {
+    bto::DevAlloc mem;        // device allocator captured at creation
     int device = 0;
     int sm_count = 0;
     int32_t nb = 0;
@@ -40,7 +43,7 @@ struct bto_ctx {
     BlockDev *blocks = nullptr;
     int32_t *perm = nullptr;
     int32_t *gblock = nullptr;
-    float *pstate = nullptr;      // [4 * slots]: x, y, z, id arrays of the particle list
+    float *pstate = nullptr;      // [4 * slots]: the particle list, units of 32 slots (x, y, z, id)
     int32_t *gcnt = nullptr;      // [slots / 32] live particles per group
     float4 *term = nullptr;
     float4 *clip = nullptr;        // [P] first outside point (xi) and stage per canonical id
@@ -80,6 +83,18 @@ struct bto_ctx {
     int32_t *derr = nullptr;        // device error flag (bounded waits)
     int32_t inject_stall = 0;       // test hook: tiled cycles left whose first wait is made to run out
 };
+
+namespace {
+
+std::mutex g_alloc_mu;
+bto::DevAlloc g_alloc;
+
+}  // namespace
+
+bto::DevAlloc bto::current_allocator() {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc;
+}
 
 namespace {
 
@@ -159,17 +174,17 @@ void brick_order(const int32_t S[3], int32_t *out) {
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 
 void free_tiling(bto_ctx *c) {
-    cudaFree(c->tiles);
-    cudaFree(c->btiles);
-    cudaFree(c->unit_tile);
-    cudaFree(c->tseed);
-    cudaFree(c->tslot);
-    cudaFree(c->tcnt0);
-    for (int k = 0; k < 2; ++k) cudaFree(c->tfront[k]);
-    for (int k = 0; k < 3; ++k) cudaFree(c->tmv[k]);
-    cudaFree(c->ocnt);
-    cudaFree(c->tact[0]);
-    cudaFree(c->tact[1]);
+    c->mem.put(c->tiles);
+    c->mem.put(c->btiles);
+    c->mem.put(c->unit_tile);
+    c->mem.put(c->tseed);
+    c->mem.put(c->tslot);
+    c->mem.put(c->tcnt0);
+    for (int k = 0; k < 2; ++k) c->mem.put(c->tfront[k]);
+    for (int k = 0; k < 3; ++k) c->mem.put(c->tmv[k]);
+    c->mem.put(c->ocnt);
+    c->mem.put(c->tact[0]);
+    c->mem.put(c->tact[1]);
     c->tiles = nullptr;
     c->btiles = nullptr;
     c->unit_tile = nullptr;
@@ -187,19 +202,19 @@ void free_tiling(bto_ctx *c) {
 void free_ctx(bto_ctx *c) {
     if (!c) return;
     free_tiling(c);
-    cudaFree(c->derr);
+    c->mem.put(c->derr);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-    cudaFree(c->blocks);
-    cudaFree(c->perm);
-    cudaFree(c->gblock);
-    cudaFree(c->pstate);
-    cudaFree(c->gcnt);
-    cudaFree(c->term);
-    cudaFree(c->clip);
-    cudaFree(c->diag_dst);
-    cudaFree(c->f4buf[0]);
-    cudaFree(c->f4buf[1]);
+    c->mem.put(c->blocks);
+    c->mem.put(c->perm);
+    c->mem.put(c->gblock);
+    c->mem.put(c->pstate);
+    c->mem.put(c->gcnt);
+    c->mem.put(c->term);
+    c->mem.put(c->clip);
+    c->mem.put(c->diag_dst);
+    c->mem.put(c->f4buf[0]);
+    c->mem.put(c->f4buf[1]);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_start) cudaEventDestroy(c->ev_start);
     for (int k = 0; k < 2; ++k) {
@@ -215,10 +230,7 @@ int group_size(const bto_ctx *c) { return 32 * c->ppt; }
 // launches).
 bto::PartList part_list(const bto_ctx *c, int64_t first = 0) {
     bto::PartList p;
-    p.x = c->pstate + first;
-    p.y = c->pstate + c->slots + first;
-    p.z = c->pstate + 2 * c->slots + first;
-    p.id = reinterpret_cast<int32_t *>(c->pstate + 3 * c->slots) + first;
+    p.rec = c->pstate + 4 * first;   // first is a multiple of 32
     p.gcnt = c->gcnt + first / group_size(c);
     return p;
 }
@@ -386,18 +398,18 @@ bto_status build_tiling(bto_ctx *c, const int32_t td[3], int nt) {
     c->mbase = mbase;
     c->obase = obase;
     c->tslots = tslots;
-    cudaError_t e = cudaMalloc(&c->tiles, sizeof(bto::TileDev) * (size_t)ntiles);
-    if (e == cudaSuccess) e = cudaMalloc(&c->btiles, sizeof(bto::BlockTiles) * (size_t)c->nb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->unit_tile, sizeof(int32_t) * std::max<size_t>(1, unit_tile.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&c->tseed, sizeof(int32_t) * (size_t)c->P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tslot, sizeof(int64_t) * (size_t)c->P);
+    cudaError_t e = c->mem.get(&c->tiles, sizeof(bto::TileDev) * (size_t)ntiles);
+    if (e == cudaSuccess) e = c->mem.get(&c->btiles, sizeof(bto::BlockTiles) * (size_t)c->nb);
+    if (e == cudaSuccess) e = c->mem.get(&c->unit_tile, sizeof(int32_t) * std::max<size_t>(1, unit_tile.size()));
+    if (e == cudaSuccess) e = c->mem.get(&c->tseed, sizeof(int32_t) * (size_t)c->P);
+    if (e == cudaSuccess) e = c->mem.get(&c->tslot, sizeof(int64_t) * (size_t)c->P);
     const size_t tb = sizeof(int32_t) * (size_t)ntiles;
-    if (e == cudaSuccess) e = cudaMalloc(&c->tcnt0, tb);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tfront[k], tb);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->tmv[k], tb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->ocnt, sizeof(int32_t) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tact[0], sizeof(float4) * (size_t)tslots);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tact[1], sizeof(float4) * (size_t)tslots);
+    if (e == cudaSuccess) e = c->mem.get(&c->tcnt0, tb);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = c->mem.get(&c->tfront[k], tb);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = c->mem.get(&c->tmv[k], tb);
+    if (e == cudaSuccess) e = c->mem.get(&c->ocnt, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = c->mem.get(&c->tact[0], sizeof(float4) * (size_t)tslots);
+    if (e == cudaSuccess) e = c->mem.get(&c->tact[1], sizeof(float4) * (size_t)tslots);
     if (e == cudaSuccess) e = cudaMemcpy(c->tiles, tiles.data(), sizeof(bto::TileDev) * (size_t)ntiles, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->btiles, bt.data(), sizeof(bto::BlockTiles) * (size_t)c->nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !unit_tile.empty())
@@ -463,6 +475,7 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
 
     bto_ctx *c = new (std::nothrow) bto_ctx();
     if (!c) return BTO_ERR_OOM;
+    c->mem = bto::current_allocator();
     c->nb = nb;
     c->P = P;
     c->slots = slots;
@@ -476,14 +489,14 @@ bto_status create_impl(int32_t nb, const int32_t *extents, const float *origins,
     for (int32_t b = 0; b < nb; ++b) brick_order(bl[(size_t)b].S, perm.data() + bl[(size_t)b].base);
 
     const size_t units = (size_t)(slots / bto::kUnit);
-    e = cudaMalloc(&c->blocks, sizeof(BlockDev) * (size_t)nb);
-    if (e == cudaSuccess) e = cudaMalloc(&c->perm, sizeof(int32_t) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->gblock, sizeof(int32_t) * units);
-    if (e == cudaSuccess) e = cudaMalloc(&c->pstate, 4 * sizeof(float) * (size_t)slots);
-    if (e == cudaSuccess) e = cudaMalloc(&c->gcnt, sizeof(int32_t) * units);
-    if (e == cudaSuccess) e = cudaMalloc(&c->term, sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->clip, sizeof(float4) * (size_t)P);
-    if (e == cudaSuccess) e = cudaMalloc(&c->derr, sizeof(int32_t));
+    e = c->mem.get(&c->blocks, sizeof(BlockDev) * (size_t)nb);
+    if (e == cudaSuccess) e = c->mem.get(&c->perm, sizeof(int32_t) * (size_t)P);
+    if (e == cudaSuccess) e = c->mem.get(&c->gblock, sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = c->mem.get(&c->pstate, 4 * sizeof(float) * (size_t)slots);
+    if (e == cudaSuccess) e = c->mem.get(&c->gcnt, sizeof(int32_t) * units);
+    if (e == cudaSuccess) e = c->mem.get(&c->term, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = c->mem.get(&c->clip, sizeof(float4) * (size_t)P);
+    if (e == cudaSuccess) e = c->mem.get(&c->derr, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->derr, 0, sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(c->blocks, bl.data(), sizeof(BlockDev) * (size_t)nb, cudaMemcpyHostToDevice);
@@ -531,6 +544,7 @@ bto_status advect_ingest(bto_ctx *c, const void *field, const void *const *field
         a.field = c->f4buf[k];
         a.fields = nullptr;
         a.p = part_list(c, B.slot_base);
+        a.err = c->derr;
         a.ngroups = region / G;
         a.term = c->term;
         a.clip = c->clip;
@@ -611,6 +625,7 @@ bto_status advect_impl(bto_ctx *c, const void *field, const void *const *fields,
     a.field = field;
     a.fields = fields;
     a.p = part_list(c);
+    a.err = c->derr;
     a.ngroups = c->slots / group_size(c);
     a.term = c->term;
     a.clip = c->clip;
@@ -668,8 +683,8 @@ bto_status bto_set_ingest(bto_ctx *ctx, int32_t enable) {
         int64_t maxn = 0;
         for (const BlockDev &B : ctx->blocks_h)
             maxn = std::max<int64_t>(maxn, (int64_t)B.nn[0] * B.nn[1] * B.nn[2]);
-        BTO_CUDA(cudaMalloc(&ctx->f4buf[0], sizeof(float4) * (size_t)maxn));
-        BTO_CUDA(cudaMalloc(&ctx->f4buf[1], sizeof(float4) * (size_t)maxn));
+        BTO_CUDA(ctx->mem.get(&ctx->f4buf[0], sizeof(float4) * (size_t)maxn));
+        BTO_CUDA(ctx->mem.get(&ctx->f4buf[1], sizeof(float4) * (size_t)maxn));
         BTO_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
         BTO_CUDA(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
         for (int k = 0; k < 2; ++k) {
@@ -775,7 +790,7 @@ bto_status bto_end_interval_ex(bto_ctx *ctx, float *d_seeds, float *d_ends, uint
     else
         BTO_CUDA(bto::launch_write_live(ctx->blocks, ctx->gblock, part_list(ctx),
                                         ctx->slots, group_size(ctx), d_ends, d_valid, d_exit_cycle,
-                                        grid, s));
+                                        grid, s, ctx->derr));
     BTO_CUDA(bto::launch_write_term(ctx->blocks, ctx->nb, ctx->P, ctx->term, d_seeds, d_ends,
                                     d_valid, d_exit_cycle, grid, s, ctx->clip, d_exit_pos, d_exit_time));
     return seed(ctx, s);
@@ -946,7 +961,7 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
     const int cyc = ctx->cycle;
     if (ctx->tiled) {
         // per-block counts, then each block's particles from its offset on
-        if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)std::max<int64_t>(ctx->nb, ctx->slots / 32)));
+        if (!ctx->diag_dst) BTO_CUDA(ctx->mem.get(&ctx->diag_dst, sizeof(int64_t) * (size_t)std::max<int64_t>(ctx->nb, ctx->slots / 32)));
         BTO_CUDA(cudaMemsetAsync(ctx->diag_dst, 0, sizeof(int64_t) * (size_t)ctx->nb, s));
         BTO_CUDA(bto::launch_count_live_tiled(ctx->blocks, ctx->nb, ctx->tiles, ctx->unit_tile, ctx->tact[cyc & 1],
                                               tile_counts(ctx, cyc), ctx->diag_dst, tiled_aux_grid(ctx), s));
@@ -982,7 +997,7 @@ bto_status bto_copy_active(bto_ctx *ctx, float *d_out, int32_t *live, bto_stream
         }
         live[b] = (int32_t)(run - B.base);
     }
-    if (!ctx->diag_dst) BTO_CUDA(cudaMalloc(&ctx->diag_dst, sizeof(int64_t) * (size_t)(ctx->slots / 32)));
+    if (!ctx->diag_dst) BTO_CUDA(ctx->mem.get(&ctx->diag_dst, sizeof(int64_t) * (size_t)(ctx->slots / 32)));
     BTO_CUDA(cudaMemcpyAsync(ctx->diag_dst, dst.data(), sizeof(int64_t) * (size_t)ng,
                              cudaMemcpyHostToDevice, s));
     BTO_CUDA(bto::launch_gather_live(part_list(ctx), ctx->diag_dst, ctx->slots,
@@ -1002,7 +1017,7 @@ bto_status bto_last_error(bto_ctx *ctx) {
         e = cudaMemcpy(&flag, ctx->derr, sizeof(int32_t), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && flag) e = cudaMemset(ctx->derr, 0, sizeof(int32_t));
         if (st == BTO_OK && e != cudaSuccess) st = cuda_status(e);
-        if (st == BTO_OK && flag) st = BTO_ERR_TIMEOUT;
+        if (st == BTO_OK && flag) st = flag == bto::kErrBounds ? BTO_ERR_BOUNDS : BTO_ERR_TIMEOUT;
     }
     ctx->sticky = BTO_OK;
     return st;
@@ -1051,6 +1066,39 @@ bto_status bto_stitch_pathlines_ex(const int32_t lattice[3], const float origin[
     return BTO_OK;
 }
 
+bto_status bto_set_device_allocator(bto_alloc_fn alloc, bto_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return BTO_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = free_fn;
+    g_alloc.user = alloc ? user : nullptr;
+    return BTO_OK;
+}
+
+int32_t bto_check_bounds_build(void) {
+#ifdef BTO_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+bto_status bto_bounds_failures(uint64_t *count, int32_t reset) {
+    if (!count) return BTO_ERR_INVALID_ARG;
+    const unsigned long long parts[3] = {bto::bounds_failures_kernels(reset != 0), bto::bounds_failures_tiled(reset != 0),
+                                         bto::bounds_failures_posthoc(reset != 0)};
+    uint64_t total = 0;
+    for (const unsigned long long v : parts) {
+        if (v == ~0ull) {
+            (void)cudaGetLastError();
+            return BTO_ERR_CUDA;
+        }
+        total += v;
+    }
+    *count = total;
+    return BTO_OK;
+}
+
 const char *bto_status_string(bto_status s) {
     switch (s) {
         case BTO_OK: return "ok";
@@ -1060,6 +1108,7 @@ const char *bto_status_string(bto_status s) {
         case BTO_ERR_OOM: return "out of memory";
         case BTO_ERR_TIMEOUT: return "bounded device wait timed out";
         case BTO_ERR_UNSUPPORTED: return "unsupported configuration";
+        case BTO_ERR_BOUNDS: return "bounds check failed (bounds-checked build)";
     }
     return "unknown status";
 }

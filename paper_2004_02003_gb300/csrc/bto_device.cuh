@@ -67,6 +67,7 @@ struct Geo {
     float fnx, fny, fnz;   // cells as float (closed-box test)
     float cmx, cmy, cmz;   // 2^23 + (cells - 1): the last cell, in the biased form of cell_coord
     uint32_t nnx, nnxy;    // node strides
+    uint32_t nodes;        // nodes of the block
 };
 
 __device__ __forceinline__ Geo load_geo(const BlockDev &B) {
@@ -78,6 +79,7 @@ __device__ __forceinline__ Geo load_geo(const BlockDev &B) {
     g.cmz = 8388608.f + (float)(g.nz - 1);
     g.nnx = (uint32_t)B.nn[0];
     g.nnxy = (uint32_t)B.nn[0] * (uint32_t)B.nn[1];
+    g.nodes = g.nnxy * (uint32_t)B.nn[2];
     return g;
 }
 
@@ -151,8 +153,11 @@ __device__ __forceinline__ float3 trilerp_packed(const PCell &C, float fx, float
 // measured slower).
 template <int LAYOUT>
 __device__ __forceinline__ void load_pcell_global(const void *__restrict__ field, uint32_t nnx, uint32_t nnxy,
-                                                  uint32_t node, PCell &C) {
+                                                  uint32_t node, PCell &C, uint32_t nodes = 0xffffffffu,
+                                                  int32_t *err = nullptr) {
     float e[4][6];
+    // the cell's last corner, node + nnx + nnxy + 1, must be a node of the block
+    if (!BTO_IN_BOUNDS((uint64_t)node + nnx + nnxy + 1 < nodes, err)) node = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t nd = node + ((q & 1) ? nnx : 0u) + ((q & 2) ? nnxy : 0u);
@@ -178,8 +183,10 @@ template <int LAYOUT>
 struct GlobalSrc {
     const void *field;
     uint32_t nnx, nnxy;
+    uint32_t nodes;   // nodes of the block (bounds-checked builds)
+    int32_t *err;     // context error word (bounds-checked builds)
     __device__ __forceinline__ void load(int, int, int, uint32_t node, PCell &C) const {
-        load_pcell_global<LAYOUT>(field, nnx, nnxy, node, C);
+        load_pcell_global<LAYOUT>(field, nnx, nnxy, node, C, nodes, err);
     }
 };
 
@@ -231,8 +238,8 @@ __device__ __forceinline__ int rk4_step_src(float3 &x, const Src &src, const Geo
 
 template <int LAYOUT>
 __device__ __forceinline__ int rk4_step(float3 &x, const void *__restrict__ field, const Geo &g,
-                                        const float3 s, float3 &q) {
-    return rk4_step_src(x, GlobalSrc<LAYOUT>{field, g.nnx, g.nnxy}, g, s, q);
+                                        const float3 s, float3 &q, int32_t *err = nullptr) {
+    return rk4_step_src(x, GlobalSrc<LAYOUT>{field, g.nnx, g.nnxy, g.nodes, err}, g, s, q);
 }
 
 // Termination location (the paper's future work, Sec. 6): the chord from the

@@ -7,6 +7,80 @@
 
 namespace bto {
 
+// Where the library's device memory comes from: the caller's allocator
+// installed with bto_set_device_allocator, else cudaMalloc / cudaFree.
+// Contexts and tapes keep the allocator that was current when they were
+// created and free through it.
+struct DevAlloc {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *user = nullptr;
+    template <class T>
+    cudaError_t get(T **p, size_t bytes) const {
+        if (!alloc) return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+        if (bytes == 0) {   // as cudaMalloc: nothing to allocate, a null pointer
+            *p = nullptr;
+            return cudaSuccess;
+        }
+        void *q = alloc(bytes, user);
+        if (q && (reinterpret_cast<uintptr_t>(q) & 255u)) {   // the contract asks for 256-byte alignment
+            release(q, user);
+            *p = nullptr;
+            return cudaErrorInvalidValue;
+        }
+        *p = static_cast<T *>(q);
+        return q ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    void put(void *p) const {
+        if (!p) return;
+        if (alloc) release(p, user);
+        else cudaFree(p);
+    }
+};
+
+// The process-wide allocator (bto_api.cu).
+DevAlloc current_allocator();
+
+// Values of a context's device error word.
+constexpr int32_t kErrTimeout = 1;   // a bounded wait gave up
+constexpr int32_t kErrBounds = 2;    // a bounds check failed (bounds-checked builds)
+
+// Bounds-checked builds (-DBTO_CHECK_BOUNDS): BTO_IN_BOUNDS(cond, err)
+// tests cond before an access; when it fails, the access is skipped, the
+// translation unit's failure counter is incremented and, when err is not
+// null, the context's error word is set to kErrBounds. Product builds
+// compile the test out (it is always true). No check traps.
+#ifdef BTO_CHECK_BOUNDS
+static __device__ unsigned long long g_bto_bounds_failures;
+__device__ __forceinline__ bool in_bounds_check(bool ok, int32_t *err) {
+    if (!ok) {
+        atomicAdd(&g_bto_bounds_failures, 1ull);
+        if (err) atomicExch(err, kErrBounds);
+    }
+    return ok;
+}
+#define BTO_IN_BOUNDS(cond, err) ::bto::in_bounds_check((cond), (err))
+#define BTO_BOUNDS_ACCESSOR(name)                                                                 \
+    unsigned long long name(bool reset) {                                                         \
+        unsigned long long v = 0;                                                                 \
+        if (cudaMemcpyFromSymbol(&v, g_bto_bounds_failures, sizeof(v)) != cudaSuccess) return ~0ull; \
+        if (reset) {                                                                              \
+            const unsigned long long z = 0;                                                       \
+            if (cudaMemcpyToSymbol(g_bto_bounds_failures, &z, sizeof(z)) != cudaSuccess) return ~0ull; \
+        }                                                                                         \
+        return v;                                                                                 \
+    }
+#else
+#define BTO_IN_BOUNDS(cond, err) true
+#define BTO_BOUNDS_ACCESSOR(name) \
+    unsigned long long name(bool) { return 0; }
+#endif
+// Failure counters of the kernels' translation units (bounds-checked
+// builds; 0 otherwise; ~0 when the counter cannot be read).
+unsigned long long bounds_failures_kernels(bool reset);
+unsigned long long bounds_failures_tiled(bool reset);
+unsigned long long bounds_failures_posthoc(bool reset);
+
 // One block of the uniform grid, as the kernels see it. Positions inside the
 // library are block-local CELL coordinates xi = (x - origin) / h, so node i
 // sits at xi = i and the block is the closed box [0, n].
@@ -30,17 +104,23 @@ struct BlockDev {
 constexpr int kRegionAlign = 128;
 constexpr int kUnit = 32;
 
-// Particle state of the untiled path, updated in place every cycle. Slot
-// i holds the position in cell units (x[i], y[i], z[i]) and the block-local
-// canonical id id[i]; the list is cut into groups of G = 32 * ppt slots,
-// and group g holds its gcnt[g] live particles in its first slots, in
-// brick order of their seeds. Positions are read and written every cycle;
-// ids move only when a group loses a particle.
+// Particle state of the untiled path, updated in place every cycle. The
+// slots come in units of 32 (kUnit); unit u holds, at rec + 128 u, the x
+// coordinates of its 32 slots, then their y, their z (cell units) and their
+// block-local canonical ids (int bits), so that a warp reads or writes one
+// field of 32 slots as one 128-byte line. The list is cut into groups of
+// G = 32 * ppt slots; group g holds its gcnt[g] live particles in its first
+// slots, in brick order of their seeds. Positions are read and written
+// every cycle; ids move only when a group loses a particle.
 struct PartList {
-    float *x, *y, *z;
-    int32_t *id;
+    float *rec;
     int32_t *gcnt;
 };
+
+// Field f (0: x, 1: y, 2: z, 3: id bits) of slot i.
+__host__ __device__ __forceinline__ int64_t part_at(int64_t i, int f) {
+    return ((i >> 5) << 7) + 32 * f + (i & 31);
+}
 
 // Arguments of one advection cycle (kernel K3: RK4 + termination + compaction).
 struct AdvectArgs {
@@ -54,6 +134,7 @@ struct AdvectArgs {
     int64_t ngroups;
     float4 *term;                // [P] termination record per canonical id
     float4 *clip;                // [P] first outside point (xi) and its RK4 stage, or NULL
+    int32_t *err;                // context error word (bounds-checked builds)
     float dt;
 };
 
@@ -167,7 +248,7 @@ cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int
                         int64_t slots, int group, PartList p, int grid, cudaStream_t s);
 cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, PartList p, int64_t slots,
                               int group, float *ends, uint8_t *valid, int32_t *exit_cycle, int grid,
-                              cudaStream_t s);
+                              cudaStream_t s, int32_t *err = nullptr);
 cudaError_t launch_gather_live(PartList p, const int64_t *dst, int64_t slots, int group, float4 *out,
                                int grid, cudaStream_t s);
 cudaError_t launch_ingest(const void *field, const void *const *fields, int b, int64_t nodes, float4 *out,

@@ -72,11 +72,13 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
     float3 s = make_float3(0.f, 0.f, 0.f);
     const void *field = nullptr;
     int64_t idbase = 0;
+    int64_t nseeds = 0;
     const PartList P = a.p;
 
     for (int64_t grp = (((int64_t)blockIdx.x * NT) + threadIdx.x) >> 5; grp < a.ngroups;
          grp += nwarps) {
-        const int cnt = __ldcg(P.gcnt + grp);
+        int cnt = __ldcg(P.gcnt + grp);
+        if (!BTO_IN_BOUNDS(cnt >= 0 && cnt <= G, a.err)) cnt = 0;
         if (cnt == 0) continue;
         const int b = BATCHED ? __ldg(a.gblock + grp * PPT) : 0;
         if (b != cur_b) {
@@ -86,14 +88,16 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
             g = load_geo(B);
             s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
             idbase = B.base;
+            nseeds = B.nseeds;
         }
         const int64_t s0 = grp * G;
         float3 r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int i = k * 32 + lane;
+            const float *u = P.rec + ((s0 >> 5) + k) * 128 + lane;
             r[k] = make_float3(0.f, 0.f, 0.f);
-            if (i < cnt) r[k] = make_float3(__ldcs(P.x + s0 + i), __ldcs(P.y + s0 + i), __ldcs(P.z + s0 + i));
+            if (i < cnt) r[k] = make_float3(__ldcs(u), __ldcs(u + 32), __ldcs(u + 64));
         }
         unsigned surv = 0;   // bit k: the lane's particle of round k survived
         bool term = false;
@@ -102,16 +106,19 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
             const int i = k * 32 + lane;
             if (i < cnt) {
                 float3 x = r[k], q;
-                const int failed = rk4_step<LAYOUT>(x, field, g, s, q);
+                const int failed = rk4_step<LAYOUT>(x, field, g, s, q, a.err);
                 if (failed == 0) {
                     r[k] = x;
                     surv |= 1u << k;
                 } else {
                     term = true;
-                    const int64_t gid = idbase + __ldcs(P.id + s0 + i);
-                    __stcs(a.term + gid, make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
-                    // first outside point and its stage; clipped at the interval end
-                    if (a.clip) __stcs(a.clip + gid, make_float4(q.x, q.y, q.z, __int_as_float(failed)));
+                    const int32_t id = __float_as_int(__ldcs(P.rec + ((s0 >> 5) + k) * 128 + 96 + lane));
+                    if (BTO_IN_BOUNDS(id >= 0 && id < nseeds, a.err)) {
+                        const int64_t gid = idbase + id;
+                        __stcs(a.term + gid, make_float4(r[k].x, r[k].y, r[k].z, __int_as_float(a.cycle)));
+                        // first outside point and its stage; clipped at the interval end
+                        if (a.clip) __stcs(a.clip + gid, make_float4(q.x, q.y, q.z, __int_as_float(failed)));
+                    }
                 }
             }
         }
@@ -119,30 +126,31 @@ __global__ void __launch_bounds__(NT, MINB) advect_kernel(const AdvectArgs a) {
             // nobody left: positions back in their slots, ids untouched
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                const int64_t i = s0 + k * 32 + lane;
+                float *u = P.rec + ((s0 >> 5) + k) * 128 + lane;
                 if (k * 32 + lane < cnt) {
-                    __stcs(P.x + i, r[k].x);
-                    __stcs(P.y + i, r[k].y);
-                    __stcs(P.z + i, r[k].z);
+                    __stcs(u, r[k].x);
+                    __stcs(u + 32, r[k].y);
+                    __stcs(u + 64, r[k].z);
                 }
             }
         } else {
             // survivors to the front of the group; every id of the group is
             // read before the first write
-            int id[PPT];
+            float id[PPT];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) id[k] = (surv >> k) & 1u ? __ldcs(P.id + s0 + k * 32 + lane) : 0;
+            for (int k = 0; k < PPT; ++k)
+                id[k] = (surv >> k) & 1u ? __ldcs(P.rec + ((s0 >> 5) + k) * 128 + 96 + lane) : 0.f;
             int kept = 0;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const bool sv = (surv >> k) & 1u;
                 const unsigned m = __ballot_sync(kFull, sv);
                 if (sv) {
-                    const int64_t j = s0 + kept + __popc(m & lt);
-                    __stcs(P.x + j, r[k].x);
-                    __stcs(P.y + j, r[k].y);
-                    __stcs(P.z + j, r[k].z);
-                    __stcs(P.id + j, id[k]);
+                    float *u = P.rec + part_at(s0 + kept + __popc(m & lt), 0);
+                    __stcs(u, r[k].x);
+                    __stcs(u + 32, r[k].y);
+                    __stcs(u + 64, r[k].z);
+                    __stcs(u + 96, id[k]);
                 }
                 kept += __popc(m);
             }
@@ -171,10 +179,11 @@ __global__ void seed_kernel(const BlockDev *__restrict__ blocks, const int32_t *
         const int32_t jx = p % B.S[0];
         const int32_t jy = (p / B.S[0]) % B.S[1];
         const int32_t jz = p / (B.S[0] * B.S[1]);
-        P.x[i] = (float)(jx * B.stride);
-        P.y[i] = (float)(jy * B.stride);
-        P.z[i] = (float)(jz * B.stride);
-        P.id[i] = p;
+        float *u = P.rec + part_at(i, 0);
+        u[0] = (float)(jx * B.stride);
+        u[32] = (float)(jy * B.stride);
+        u[64] = (float)(jz * B.stride);
+        u[96] = __int_as_float(p);
     }
 }
 
@@ -182,15 +191,19 @@ __global__ void seed_kernel(const BlockDev *__restrict__ blocks, const int32_t *
 __global__ void write_live_kernel(const BlockDev *__restrict__ blocks,
                                   const int32_t *__restrict__ gblock, const PartList P,
                                   int64_t slots, int group, float *__restrict__ ends,
-                                  uint8_t *__restrict__ valid, int32_t *__restrict__ exit_cycle) {
+                                  uint8_t *__restrict__ valid, int32_t *__restrict__ exit_cycle,
+                                  int32_t *__restrict__ err) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
         if (i % group >= P.gcnt[i / group]) continue;
         const BlockDev &B = blocks[gblock[i / kUnit]];
-        const int64_t gid = B.base + P.id[i];
-        ends[3 * gid + 0] = fmaf(P.x[i], B.h[0], B.origin[0]);
-        ends[3 * gid + 1] = fmaf(P.y[i], B.h[1], B.origin[1]);
-        ends[3 * gid + 2] = fmaf(P.z[i], B.h[2], B.origin[2]);
+        const float *u = P.rec + part_at(i, 0);
+        const int32_t id = __float_as_int(u[96]);
+        if (!BTO_IN_BOUNDS(id >= 0 && id < B.nseeds, err)) continue;
+        const int64_t gid = B.base + id;
+        ends[3 * gid + 0] = fmaf(u[0], B.h[0], B.origin[0]);
+        ends[3 * gid + 1] = fmaf(u[32], B.h[1], B.origin[1]);
+        ends[3 * gid + 2] = fmaf(u[64], B.h[2], B.origin[2]);
         if (valid) valid[gid] = 1;
         if (exit_cycle) exit_cycle[gid] = -1;
     }
@@ -260,7 +273,10 @@ __global__ void gather_live_kernel(const PartList P, const int64_t *__restrict__
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
         const int64_t g = i / group;
         const int k = (int)(i % group);
-        if (k < P.gcnt[g]) out[dst[g] + k] = make_float4(P.x[i], P.y[i], P.z[i], __int_as_float(P.id[i]));
+        if (k < P.gcnt[g]) {
+            const float *u = P.rec + part_at(i, 0);
+            out[dst[g] + k] = make_float4(u[0], u[32], u[64], u[96]);
+        }
     }
 }
 
@@ -325,6 +341,8 @@ cudaError_t occ_t(size_t dyn, int *n) {
 
 }  // namespace
 
+BTO_BOUNDS_ACCESSOR(bounds_failures_kernels)
+
 cudaError_t launch_advect(const AdvectArgs &a, int layout, int nt, int ppt, bool cap, int grid,
                           size_t dyn, cudaStream_t s) {
     const bool batched = a.nb > 1;
@@ -360,8 +378,8 @@ cudaError_t launch_seed(const BlockDev *blocks, const int32_t *gblock, const int
 
 cudaError_t launch_write_live(const BlockDev *blocks, const int32_t *gblock, PartList p, int64_t slots,
                               int group, float *ends, uint8_t *valid, int32_t *exit_cycle, int grid,
-                              cudaStream_t s) {
-    write_live_kernel<<<grid, 256, 0, s>>>(blocks, gblock, p, slots, group, ends, valid, exit_cycle);
+                              cudaStream_t s, int32_t *err) {
+    write_live_kernel<<<grid, 256, 0, s>>>(blocks, gblock, p, slots, group, ends, valid, exit_cycle, err);
     return cudaGetLastError();
 }
 

@@ -8,12 +8,14 @@
 // that state in a fixed-size array that lives in the library's own device
 // image instead. The caller still passes the fields and the output buffers.
 //
-// The scratch array below is a file-scope __device__ variable: every device
-// that loads the library holds its BTO_NOALLOC_SCRATCH_BYTES until the
-// process exits, and every call on that device shares it. Host code cannot
-// use the array's name as a device address; the first call on each device
-// asks the runtime for the array's device address (cudaGetSymbolAddress,
-// with that device current) and keeps it for later calls.
+// The scratch array below is a file-scope __device__ variable of this
+// translation unit's device module. Under the runtime's lazy module loading
+// the module, and with it the array's BTO_NOALLOC_SCRATCH_BYTES, is loaded
+// on a device by the first call made there; it stays until the process
+// exits, and every call on that device shares it. Host code cannot use the
+// array's name as a device address; the first call on each device asks the
+// runtime for the array's device address (cudaGetSymbolAddress, with that
+// device current) and keeps it for later calls.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -33,7 +35,7 @@ constexpr int64_t kMaxSlots = (kMaxSeeds + bto::kRegionAlign - 1) / bto::kRegion
 constexpr int64_t kMaxUnits = kMaxSlots / bto::kUnit;
 
 // Byte offsets of the parts of the scratch array (each 256-byte aligned):
-// the particle list (x, y, z and id arrays), the termination records, the
+// the particle list (units of 32 slots: x, y, z, id), the termination records, the
 // group counts, the seed order, the 32-slot-unit block map and the block.
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffPart = 0;
@@ -139,10 +141,7 @@ extern "C" bto_status bto_interval_noalloc(const int32_t extent_cells[3], const 
     const int64_t slots = (B.nseeds + bto::kRegionAlign - 1) / bto::kRegionAlign * bto::kRegionAlign;
     const int nt = 128, ppt = 2, group = 32 * ppt;
     bto::PartList part;
-    part.x = reinterpret_cast<float *>(base + kOffPart);
-    part.y = part.x + slots;
-    part.z = part.y + slots;
-    part.id = reinterpret_cast<int32_t *>(part.z + slots);
+    part.rec = reinterpret_cast<float *>(base + kOffPart);
     part.gcnt = reinterpret_cast<int32_t *>(base + kOffGcnt);
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -49,7 +49,8 @@ __global__ void fill_lattice_kernel(int3 S, const float *__restrict__ ends, cons
             if (status) status[p] = 0;
             continue;
         }
-        const int64_t pl = p - best_a * step[best_axis], pr = p + best_b * step[best_axis];
+        int64_t pl = p - best_a * step[best_axis], pr = p + best_b * step[best_axis];
+        if (!BTO_IN_BOUNDS(pl >= 0 && pr < P, nullptr)) pl = pr = p;
         const float wl = (float)best_b / (float)(best_a + best_b), wr = (float)best_a / (float)(best_a + best_b);
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[3 * p + k] = wl * ends[3 * pl + k] + wr * ends[3 * pr + k];
@@ -77,6 +78,8 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
                               const float *__restrict__ start, float *__restrict__ path) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float nan = __int_as_float(0x7fc00000);
+    const int64_t P = (int64_t)S.x * S.y * S.z;
+    (void)P;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += stride) {
         float x = start[3 * i], y = start[3 * i + 1], z = start[3 * i + 2];
         path[3 * i] = x; path[3 * i + 1] = y; path[3 * i + 2] = z;
@@ -106,7 +109,8 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
                     for (int m = 0; m < 4; ++m) {
                         if (m > 0) j[ax[m - 1]] = min(j[ax[m - 1]] + 1, ext[ax[m - 1]] - 1);
                         const float wgt = m == 0 ? 1.f - t[0] : (m == 3 ? t[2] : t[m - 1] - t[m]);
-                        const int64_t p = j[0] + (int64_t)S.x * (j[1] + (int64_t)S.y * j[2]);
+                        int64_t p = j[0] + (int64_t)S.x * (j[1] + (int64_t)S.y * j[2]);
+                        if (!BTO_IN_BOUNDS(p >= 0 && p < P, nullptr)) p = 0;
 #pragma unroll
                         for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
                     }
@@ -119,7 +123,8 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
                             for (int a = 0; a < 2; ++a) {
                                 const int jx = min(ix + a, S.x - 1), jy = min(iy + b, S.y - 1), jz = min(iz + c, S.z - 1);
                                 const float wgt = (a ? fx : 1.f - fx) * (b ? fy : 1.f - fy) * (c ? fz : 1.f - fz);
-                                const int64_t p = jx + (int64_t)S.x * (jy + (int64_t)S.y * jz);
+                                int64_t p = jx + (int64_t)S.x * (jy + (int64_t)S.y * jz);
+                                if (!BTO_IN_BOUNDS(p >= 0 && p < P, nullptr)) p = 0;
 #pragma unroll
                                 for (int d = 0; d < 3; ++d) acc[d] = fmaf(wgt, E[3 * p + d], acc[d]);
                             }
@@ -134,6 +139,8 @@ __global__ void stitch_kernel(int3 S, float3 origin, float3 inv_sp, int32_t inte
 }
 
 }  // namespace
+
+BTO_BOUNDS_ACCESSOR(bounds_failures_posthoc)
 
 cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
                           const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,

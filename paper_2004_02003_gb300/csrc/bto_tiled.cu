@@ -142,6 +142,8 @@ struct BoxSrc {
     uint32_t cx, cy, cz;   // cells of the box per axis (staged nodes - 1)
     int my, pitch;         // rows per z plane, floats per row
     uint32_t d0, dy, dz;   // F3 row misalignment: (d0 + j dy + k dz) mod 4 floats
+    uint32_t nodes;        // nodes of the block (bounds-checked builds)
+    int32_t *err;          // context error word (bounds-checked builds)
 
     __device__ __forceinline__ void load(int ix, int iy, int iz, uint32_t node, PCell &C) const {
         const uint32_t xo = (uint32_t)(ix - lox), j = (uint32_t)(iy - loy), k = (uint32_t)(iz - loz);
@@ -165,7 +167,7 @@ struct BoxSrc {
             }
             pcell_set(C, e[0], e[1], e[2], e[3]);
         } else {
-            load_pcell_global<LAYOUT>(field, nnx, nnxy, node, C);
+            load_pcell_global<LAYOUT>(field, nnx, nnxy, node, C, nodes, err);
         }
     }
 };
@@ -282,6 +284,7 @@ __device__ __forceinline__ void append_mover(const TiledArgs &a, const BlockTile
     cell_coord(r.y, g.cmy, iy, f);
     cell_coord(r.z, g.cmz, iz, f);
     const int dest = bt.first + (ix >> a.tsh[0]) + bt.nt[0] * ((iy >> a.tsh[1]) + bt.nt[1] * (iz >> a.tsh[2]));
+    if (!BTO_IN_BOUNDS(dest >= 0 && dest < a.ntiles, a.err)) return;
     const int q = atomicAdd(a.movein_out + dest, 1);
     if (q < a.cm) __stcs(a.out + a.mbase + (int64_t)dest * a.cm + q, r);
     else append_overflow(a, r);
@@ -301,7 +304,7 @@ __device__ void advect_overflow(const TiledArgs &a, int nwarps_cta) {
         const Geo g = load_geo(B);
         const float3 s = make_float3(a.dt * B.inv_h[0], a.dt * B.inv_h[1], a.dt * B.inv_h[2]);
         float3 x = make_float3(r.x, r.y, r.z), q;
-        const int failed = rk4_step<LAYOUT>(x, block_field(a, b), g, s, q);
+        const int failed = rk4_step<LAYOUT>(x, block_field(a, b), g, s, q, a.err);
         if (failed == 0) {
             r.x = x.x; r.y = x.y; r.z = x.z;
             append_mover(a, a.btiles[b], g, r);
@@ -394,6 +397,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) advect_tiled_kernel(const Tiled
             src.field = block_field(a, cur_b);
             src.nnx = g.nnx;
             src.nnxy = g.nnxy;
+            src.nodes = g.nodes;
+            src.err = a.err;
             src.dy = (3u * g.nnx) & 3u;
             src.dz = (3u * g.nnxy) & 3u;
         }
@@ -617,6 +622,8 @@ cudaError_t tiled_launch_t(const TiledArgs &a, int grid, size_t smem, cudaStream
 }
 
 }  // namespace
+
+BTO_BOUNDS_ACCESSOR(bounds_failures_tiled)
 
 size_t tiled_box_bytes(int layout, const int32_t tdim[3], int32_t *pitch, int32_t *box_floats) {
     const int64_t mx = (int64_t)tdim[0] + 3;
