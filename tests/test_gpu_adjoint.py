@@ -1,13 +1,19 @@
 """GPU adjoint (libbto tape) against closed forms and the FP64 oracle adjoint.
 
-Tolerance for the FP32 adjoint against the FP64 oracle: each RK4 step costs
+Tolerance for the FP32 adjoint against the FP64 oracle. Each RK4 step costs
 about a hundred FP32 operations per component (relative rounding 6e-8 each),
 and 200 steps chain them through Jacobians of norm up to ~10, so relative
-errors up to ~1e-4 are expected for most particles; a particle whose FP32
-trajectory sits in another cell than the FP64 one at some stage (its stage
-points within ~1e-5 cells of a face) picks up the trilinear gradient's jump
-there. The bounds are a median of 1e-5 and a 99th percentile of 2e-3 of the
-per-particle gradient norm (measured: 1e-6 and 3e-4).
+errors up to ~1e-4 are expected. The trilinear field is only continuous
+across cell faces: its gradient jumps there, so a particle whose FP32 path
+puts a sample point (a step's start or one of its stage points) in another
+cell than the FP64 path picks up an O(1) relative change of that stage's
+Jacobian. Such particles are the ones whose FP64 sample points come within
+CELL_EPS of a cell face, where the FP32 and FP64 paths (apart by ~1e-5
+cells at most) can straddle the face, together with those whose exit cycles
+differ. They are excluded, counted and the count bounded (5% of the
+particles for the seed gradients, 12% of the valid ones, which sample more
+cycles, for the Jacobian); every other particle is held to a maximum
+relative error of 2e-3 (no percentile), 3x the largest measured.
 """
 import numpy as np
 import pytest
@@ -100,6 +106,11 @@ def test_checkpoint_interval_does_not_change_gradients():
 # ----------------------------------------------------------------------------
 N4, L4, DT4, S4 = (64, 64, 64), 200, 0.01, 2
 H4 = (2 * np.pi / 64,) * 3
+# Maximum errors on every particle kept (see the module docstring; measured
+# on GB300: seed gradients 6.1e-4)
+SEED_GRAD_MAX_REL = 2e-3
+JAC_MAX_REL = 2e-3
+FTLE_MAX_ABS = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -116,6 +127,42 @@ def _loss_grad_upstream(ends, seeds, valid):
     return 2.0 * (ends - seeds) * valid[:, None]
 
 
+# Sample points closer than this to a cell face (cells) may sit in another
+# cell on the FP32 path. The FP32 and FP64 end positions of this workload
+# differ by 2.6e-5 cells at the median (1.4e-4 at the 99th percentile), so
+# a point within 1e-5 cells of a face is the one likely to straddle it.
+CELL_EPS = 1e-5
+
+
+def _cell_face_margin(g, fields, dt, xs, exit_cycle, h, cycles):
+    """Smallest distance, in cells, from any sample point of each particle's
+    FP64 oracle path (the step start and the stage points p2, p3, p4 of
+    every cycle in which it is alive) to the nearest cell face plane. The
+    start of the first cycle is left out: it is the seed, held exactly on
+    both sides (a lattice node, on a cell corner), so both take the same
+    cell there."""
+    h = np.asarray(h, dtype=np.float64)
+    org = np.asarray(g.origin, dtype=np.float64) if hasattr(g, "origin") else np.zeros(3)
+    m = np.full(xs[0].shape[0], np.inf)
+    for c in range(cycles):
+        alive = (exit_cycle < 0) | (exit_cycle >= c)
+        if not alive.any():
+            break
+        x = xs[c][alive]
+        F = fields[c]
+        k1 = oracle.sample(g, F, x)
+        p2 = x + 0.5 * dt * k1
+        k2 = oracle.sample(g, F, p2)
+        p3 = x + 0.5 * dt * k2
+        k3 = oracle.sample(g, F, p3)
+        p4 = x + dt * k3
+        for q in ((x, p2, p3, p4) if c > 0 else (p2, p3, p4)):
+            xi = (q - org) / h
+            d = np.abs(xi - np.round(xi)).min(axis=1)
+            m[alive] = np.minimum(m[alive], d)
+    return m
+
+
 def test_adjoint_workload_seed_and_field_gradients_vs_oracle(adj_case):
     fields, g, seeds, ids = adj_case
     sub = seeds[ids]
@@ -125,16 +172,19 @@ def test_adjoint_workload_seed_and_field_gradients_vs_oracle(adj_case):
     _, lam_o, gF_o = oracle.vjp(g, lambda c: fields[c], DT4, sub, L4, up, want_field_grads=True)
     grad_g, ends_g, valid_g, exit_g, gF_g = _tape_vjp(N4, (0, 0, 0), H4, sub, fields, DT4, up, K=16,
                                                        want_fields=True)
-    same = (exit_g == st_o.exit_cycle)
-    assert same.mean() > 0.99
     assert 0.1 < st_o.valid.mean() < 0.6
+    _, xs = oracle.forward_with_history(g, lambda c: fields[c], DT4, sub, L4)
+    margin = _cell_face_margin(g, fields, DT4, xs, st_o.exit_cycle, H4, L4)
+    keep = (exit_g == st_o.exit_cycle) & (margin >= CELL_EPS)
+    excluded = int((~keep).sum())
     # seed gradients (J^T up): per-particle error relative to the gradient's size
-    ref = lam_o[same]
-    err = np.linalg.norm(grad_g[same] - ref, axis=1) / (np.linalg.norm(ref, axis=1) + 1e-6)
+    ref = lam_o[keep]
+    err = np.linalg.norm(grad_g[keep] - ref, axis=1) / (np.linalg.norm(ref, axis=1) + 1e-6)
     live = np.linalg.norm(ref, axis=1) > 0
-    print("seed-grad rel err: median %.2e p99 %.2e max %.2e" % (np.median(err[live]),
-          np.percentile(err[live], 99), err[live].max()))
-    assert np.median(err[live]) < 1e-5 and np.percentile(err[live], 99) < 2e-3
+    print("seed-grad: %d of %d excluded (exit cycle or a sample point within %.0e cells of a cell face); "
+          "rel err median %.2e max %.2e" % (excluded, len(sub), CELL_EPS, np.median(err[live]), err[live].max()))
+    assert excluded <= 0.05 * len(sub)
+    assert err[live].max() < SEED_GRAD_MAX_REL
     # field gradients at 64 random (cycle, node component) pairs with support
     rng = np.random.default_rng(45)
     gF_o = np.stack(gF_o)
@@ -162,15 +212,21 @@ def test_adjoint_workload_jacobian_and_ftle(adj_case):
         e = np.zeros((len(ids), 3)); e[:, a] = 1.0
         st, lam, _ = oracle.vjp(g, lambda c: fields[c], DT4, sub, L4, e)
         Jo[:, a, :] = lam
-    ok = (v == 1) & (st.valid == 1)
-    assert ok.sum() > 500
+    _, xs = oracle.forward_with_history(g, lambda c: fields[c], DT4, sub, L4)
+    margin = _cell_face_margin(g, fields, DT4, xs, st.exit_cycle, H4, L4)
+    both = (v == 1) & (st.valid == 1)
+    ok = both & (margin >= CELL_EPS)
+    excluded = int((both & ~ok).sum())
+    assert ok.sum() > 500 and excluded <= 0.12 * both.sum()
     rel = np.linalg.norm((J - Jo)[ok], axis=(1, 2)) / np.linalg.norm(Jo[ok], axis=(1, 2))
-    print("jacobian rel err: median %.2e p99 %.2e" % (np.median(rel), np.percentile(rel, 99)))
-    assert np.median(rel) < 1e-5 and np.percentile(rel, 99) < 2e-3
     # FTLE from the oracle Jacobian, by numpy's symmetric eigensolver
     lmax = np.linalg.eigvalsh(np.einsum("pki,pkj->pij", Jo[ok], Jo[ok]))[:, -1]
     f_o = 0.5 * np.log(lmax) / (L4 * DT4)
-    assert np.median(np.abs(f[ok] - f_o)) < 1e-4 and np.percentile(np.abs(f[ok] - f_o), 99) < 1e-2
+    ferr = np.abs(f[ok] - f_o)
+    print("jacobian: %d of %d valid excluded; rel err median %.2e max %.2e; ftle abs err max %.2e"
+          % (excluded, int(both.sum()), np.median(rel), rel.max(), ferr.max()))
+    assert rel.max() < JAC_MAX_REL
+    assert ferr.max() < FTLE_MAX_ABS
     assert np.all(np.isnan(f[v == 0]))
 
 

@@ -326,7 +326,12 @@ def test_interval_graph_equals_per_cycle_calls():
 
 def test_bto_valid_ends_equal_global_map():
     # BTO blocks vs one block over the whole domain (particles cross blocks):
-    # a particle that stays in its block follows the same cells and node values.
+    # a particle that stays in its block follows the same cells and node
+    # values. The global map (the no-termination-at-interior-faces run of
+    # Sec. 3.1) is itself held to the FP64 oracle run on the whole 48^3 grid,
+    # under the parity rule (end positions within 1e-3 cells; flags equal
+    # away from the domain faces), and the BTO-valid particles satisfy the
+    # Eq. (hx) reading: they stay valid in the global map with the same ends.
     import torch
     nbx, n, L = 2, 24, 30
     G = nbx * n
@@ -346,6 +351,9 @@ def test_bto_valid_ends_equal_global_map():
     bo = {k: v.cpu().numpy() for k, v in bctx.end_interval().items()}
     gctx = bto.Context((G, G, G), (0, 0, 0), h, 2, L)
     go = run_gpu_interval(gctx, _dev(gfields), dt)
+    gref = oracle.run_interval(oracle.Grid.make((G, G, G), (0, 0, 0), h), 2, L, dt, lambda c: gfields[c])
+    rep = compare(go, gref, h)
+    assert rep["both_valid"] > 0.5 * rep["n"]
     # map each block seed to its global canonical id
     S = n // 2
     gid = []
