@@ -76,6 +76,8 @@ def _load():
     lib.bto_oracle_adjoint_cycle.argtypes = [fp, i64p, dp, dp, ctypes.c_double, ctypes.c_int64, dp, u8p, dp,
                                              dp, ctypes.c_int32]
     lib.bto_oracle_adjoint_cycle.restype = None
+    lib.bto_oracle_delaunay.argtypes = [i64p, u8p, ctypes.c_int64, i32p]
+    lib.bto_oracle_delaunay.restype = ctypes.c_int64
     lib.bto_oracle_max_threads.argtypes = []
     lib.bto_oracle_max_threads.restype = ctypes.c_int32
     _lib = lib
@@ -374,6 +376,75 @@ def stitch(S, origin, spacing, ends_list, start, scheme: str = "trilinear"):
 # ---------------------------------------------------------------------------
 # Accuracy metrics (Sec. 4.3): b = BTO positions, m = reference positions.
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Post hoc reconstruction over a Delaunay triangulation (Sec. 3.2)
+# ---------------------------------------------------------------------------
+def delaunay(S, valid: np.ndarray) -> np.ndarray:
+    """Delaunay triangulation (Bowyer-Watson, exact predicates, ties broken
+    by the lifted-weight perturbation described in bto_oracle.c) of the
+    valid points of the seed lattice S (x fastest). Returns (T, 4) canonical
+    lattice ids, each tetrahedron positively oriented."""
+    lib = _load()
+    S64 = np.asarray(S, dtype=np.int64)
+    v = np.ascontiguousarray(np.asarray(valid).reshape(-1), dtype=np.uint8)
+    cap = 16 * int(v.sum()) + 64
+    out = np.empty((cap, 4), dtype=np.int32)
+    nt = lib.bto_oracle_delaunay(_ptr(S64, ctypes.c_int64), _ptr(v, ctypes.c_uint8), cap,
+                                 _ptr(out, ctypes.c_int32))
+    if nt < 0:
+        raise RuntimeError(f"bto_oracle_delaunay failed ({nt})")
+    return out[:nt].copy()
+
+
+def lattice_coords(S, ids: np.ndarray) -> np.ndarray:
+    S = [int(v) for v in S]
+    ids = np.asarray(ids, dtype=np.int64)
+    return np.stack([ids % S[0], (ids // S[0]) % S[1], ids // (S[0] * S[1])], axis=-1).astype(np.float64)
+
+
+def delaunay_interpolate(S, tets: np.ndarray, ends: np.ndarray, q: np.ndarray, tol: float = 1e-9):
+    """Barycentric interpolation of the end positions over the tetrahedron
+    of ``tets`` that holds each query point q (lattice coordinates, (m, 3)).
+    Returns (values (m, 3), found (m,) bool); a point held by no tetrahedron
+    (outside the hull of the valid points) gets NaN."""
+    E = np.asarray(ends, dtype=np.float64).reshape(-1, 3)
+    V = lattice_coords(S, tets)                       # (T, 4, 3)
+    A = np.transpose(V[:, 1:, :] - V[:, :1, :], (0, 2, 1))   # columns v1 - v0, v2 - v0, v3 - v0
+    Ainv = np.linalg.inv(A)
+    q = np.asarray(q, dtype=np.float64).reshape(-1, 3)
+    vals = np.full((q.shape[0], 3), np.nan)
+    found = np.zeros(q.shape[0], dtype=bool)
+    for i in range(q.shape[0]):
+        l123 = np.einsum("tij,tj->ti", Ainv, q[i] - V[:, 0, :])
+        lam = np.concatenate([1.0 - l123.sum(axis=1, keepdims=True), l123], axis=1)
+        hit = np.flatnonzero(np.all(lam >= -tol, axis=1))
+        if hit.size == 0:
+            continue
+        t = hit[0]
+        vals[i] = lam[t] @ E[tets[t]]
+        found[i] = True
+    return vals, found
+
+
+def fill_delaunay(S, ends: np.ndarray, valid: np.ndarray):
+    """Reconstruction of the missing basis flows of a seed lattice over the
+    Delaunay triangulation of the valid ones (Sec. 3.2): each missing entry
+    takes the barycentric interpolant at its own lattice point. Returns
+    (filled ends, status: 1 valid, 2 filled, 0 missing)."""
+    v = np.asarray(valid).reshape(-1).astype(bool)
+    E = np.asarray(ends, dtype=np.float64).reshape(-1, 3).copy()
+    status = np.where(v, 1, 0).astype(np.uint8)
+    miss = np.flatnonzero(~v)
+    if miss.size and v.sum() >= 4:
+        tets = delaunay(S, v)
+        vals, found = delaunay_interpolate(S, tets, E, lattice_coords(S, miss))
+        E[miss] = vals
+        status[miss[found]] = 2
+    else:
+        E[miss] = np.nan
+    return E, status
+
+
 def total_average_l2(b: np.ndarray, m: np.ndarray) -> float:
     """Total average L2 norm, (1/p) sum_i ||b_i - m_i|| (Sec. 4.3). The sum
     runs over the p particles (the printed bounds i = 0..p are read as the p

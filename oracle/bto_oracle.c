@@ -50,6 +50,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -385,4 +386,252 @@ ORACLE_API int32_t bto_oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Post hoc reconstruction over a Delaunay triangulation (Sec. 3.2): the
+ * start locations of the valid basis flows are triangulated, and a point of
+ * the domain takes the barycentric interpolant of the end positions at the
+ * vertices of the tetrahedron that holds it.
+ *
+ * Points are seed-lattice indices j (integers); the triangulation is built
+ * by the Bowyer-Watson algorithm (Bowyer 1981; Watson 1981): points are
+ * inserted one at a time; the tetrahedra whose circumsphere holds the new
+ * point are removed, and the new point is joined to the faces of the cavity
+ * they leave. A large enclosing tetrahedron of four extra points starts the
+ * triangulation and its tetrahedra are dropped at the end.
+ *
+ * Predicates are exact (integer arithmetic in 128 bits). The paper does not
+ * say how its triangulation chooses among the Delaunay triangulations of
+ * cospherical points (lattice cells are cospherical in eights). Reading:
+ * the triangulation is the lower convex hull of the points lifted to
+ * w(j) = |j|^2 + d_r(j), where d_0 >> d_1 >> ... > 0 are infinitesimal and
+ * r(j) is the point's rank (canonical lattice id, x fastest; the enclosing
+ * points rank last). A point e is inside the circumsphere of the tetrahedron
+ * (a, b, c, d) when the sign of the 5x5 determinant of the rows
+ * (x, y, z, w, 1) says so; when the unperturbed determinant is zero, the
+ * term of the lowest-ranked point whose cofactor is not zero decides.
+ * --------------------------------------------------------------------------- */
+typedef __int128 i128;
+
+typedef struct {
+    int64_t x[3];
+    int64_t rank;
+} dpt;
+
+static i128 det3_128(i128 a0, i128 a1, i128 a2, i128 b0, i128 b1, i128 b2, i128 c0, i128 c1, i128 c2)
+{
+    return a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+}
+
+/* orientation of (a, b, c, d): det of the rows b - a, c - a, d - a */
+static i128 orient3(const dpt *a, const dpt *b, const dpt *c, const dpt *d)
+{
+    return det3_128(b->x[0] - a->x[0], b->x[1] - a->x[1], b->x[2] - a->x[2],
+                    c->x[0] - a->x[0], c->x[1] - a->x[1], c->x[2] - a->x[2],
+                    d->x[0] - a->x[0], d->x[1] - a->x[1], d->x[2] - a->x[2]);
+}
+
+/* 4x4 determinant by expansion along the last column */
+static i128 det4_128(const i128 m[4][4])
+{
+    i128 r = 0;
+    for (int i = 0; i < 4; ++i) {
+        i128 s[3][3];
+        for (int k = 0, rr = 0; k < 4; ++k) {
+            if (k == i) continue;
+            for (int c = 0; c < 3; ++c) s[rr][c] = m[k][c];
+            ++rr;
+        }
+        const i128 minor = det3_128(s[0][0], s[0][1], s[0][2], s[1][0], s[1][1], s[1][2], s[2][0], s[2][1], s[2][2]);
+        r += ((i + 3) % 2 ? -1 : 1) * m[i][3] * minor;
+    }
+    return r;
+}
+
+/* The 5x5 determinant of the rows (x, y, z, w, 1) of p[0..4] with the lifted
+ * weights w = |x|^2 + d_rank: its sign, the infinitesimals resolving a zero. */
+static int lifted_sign(const dpt *const p[5])
+{
+    /* unperturbed part, translated so that p[4] is the origin (the last
+     * column then leaves the 4x4 determinant of the first four rows) */
+    i128 m[4][4];
+    for (int i = 0; i < 4; ++i) {
+        i128 s = 0;
+        for (int a = 0; a < 3; ++a) {
+            m[i][a] = (i128)(p[i]->x[a] - p[4]->x[a]);
+            s += m[i][a] * m[i][a];
+        }
+        m[i][3] = s;
+    }
+    const i128 d0 = det4_128(m);
+    if (d0 != 0) return d0 > 0 ? 1 : -1;
+    /* d_r term of row i: (-1)^(i + 3) times the determinant of the rows
+     * (x, y, z, 1) of the other four points (0-based rows, w in column 3) */
+    int order[5] = {0, 1, 2, 3, 4};
+    for (int i = 1; i < 5; ++i)
+        for (int k = i; k > 0 && p[order[k]]->rank < p[order[k - 1]]->rank; --k) {
+            const int t = order[k]; order[k] = order[k - 1]; order[k - 1] = t;
+        }
+    for (int oi = 0; oi < 5; ++oi) {
+        const int i = order[oi];
+        const dpt *q[4];
+        for (int k = 0, r = 0; k < 5; ++k)
+            if (k != i) q[r++] = p[k];
+        /* det of rows (x, y, z, 1) = -orient3(q0, q1, q2, q3) */
+        const i128 o = -orient3(q[0], q[1], q[2], q[3]);
+        if (o != 0) {
+            const i128 c = ((i + 3) % 2 ? -o : o);
+            return c > 0 ? 1 : -1;
+        }
+    }
+    return 0;
+}
+
+/* e strictly inside the circumsphere of the positively oriented (a, b, c, d) */
+static int in_sphere(const dpt *a, const dpt *b, const dpt *c, const dpt *d, const dpt *e)
+{
+    const dpt *p[5] = {a, b, c, d, e};
+    return lifted_sign(p) < 0;
+}
+
+typedef struct {
+    int32_t v[4];
+} dtet;
+
+typedef struct {
+    int32_t v[3];     /* sorted vertex ids */
+    int32_t o[3];     /* the face's vertices in the order of its tetrahedron's listing */
+    int32_t count;
+} dface;
+
+static int face_cmp(const void *pa, const void *pb)
+{
+    const dface *a = (const dface *)pa, *b = (const dface *)pb;
+    for (int k = 0; k < 3; ++k)
+        if (a->v[k] != b->v[k]) return a->v[k] < b->v[k] ? -1 : 1;
+    return 0;
+}
+
+/* Delaunay triangulation of the valid points of the lattice S (x fastest).
+ * Writes at most cap tetrahedra as canonical lattice ids (each positively
+ * oriented) and returns their number; -1: cap too small or allocation
+ * failed; -2: a degenerate cavity (never expected with exact predicates). */
+ORACLE_API int64_t bto_oracle_delaunay(const int64_t S[3], const uint8_t *valid, int64_t cap, int32_t *tets)
+{
+    const int64_t P = S[0] * S[1] * S[2];
+    int64_t n = 0;
+    for (int64_t i = 0; i < P; ++i) n += valid[i] != 0;
+    dpt *pts = (dpt *)malloc(sizeof(dpt) * (size_t)(n + 4));
+    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 4));
+    if (!pts || !ids) { free(pts); free(ids); return -1; }
+    int64_t k = 0;
+    for (int64_t i = 0; i < P; ++i) {
+        if (!valid[i]) continue;
+        pts[k].x[0] = i % S[0];
+        pts[k].x[1] = (i / S[0]) % S[1];
+        pts[k].x[2] = i / (S[0] * S[1]);
+        pts[k].rank = i;
+        ids[k] = i;
+        ++k;
+    }
+    /* enclosing tetrahedron: vertices 2^20 away from the lattice's centre */
+    const int64_t B = (int64_t)1 << 20;
+    const int64_t cx = S[0] / 2, cy = S[1] / 2, cz = S[2] / 2;
+    const int64_t dir[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+    for (int q = 0; q < 4; ++q) {
+        pts[n + q].x[0] = cx + 3 * B * dir[q][0];
+        pts[n + q].x[1] = cy + 3 * B * dir[q][1];
+        pts[n + q].x[2] = cz + 3 * B * dir[q][2];
+        pts[n + q].rank = P + q;
+        ids[n + q] = -1;
+    }
+    int64_t tcap = 64 + 8 * (n + 4), nt = 0;
+    dtet *T = (dtet *)malloc(sizeof(dtet) * (size_t)tcap);
+    uint8_t *alive = (uint8_t *)malloc((size_t)tcap);
+    if (!T || !alive) { free(pts); free(ids); free(T); free(alive); return -1; }
+    {
+        dtet t0 = {{(int32_t)n, (int32_t)(n + 1), (int32_t)(n + 2), (int32_t)(n + 3)}};
+        if (orient3(&pts[n], &pts[n + 1], &pts[n + 2], &pts[n + 3]) < 0) {
+            const int32_t s = t0.v[0]; t0.v[0] = t0.v[1]; t0.v[1] = s;
+        }
+        T[0] = t0;
+        alive[0] = 1;
+        nt = 1;
+    }
+    int64_t status = 0;
+    dface *faces = NULL;
+    int64_t fcap = 0;
+    for (int64_t ip = 0; ip < n && status == 0; ++ip) {
+        const dpt *e = &pts[ip];
+        /* the cavity: every tetrahedron whose circumsphere holds the point */
+        int64_t nf = 0;
+        for (int64_t t = 0; t < nt; ++t) {
+            if (!alive[t]) continue;
+            const dtet *tt = &T[t];
+            if (!in_sphere(&pts[tt->v[0]], &pts[tt->v[1]], &pts[tt->v[2]], &pts[tt->v[3]], e)) continue;
+            alive[t] = 0;
+            if (nf + 4 > fcap) {
+                fcap = 2 * (nf + 4) + 64;
+                dface *nfaces = (dface *)realloc(faces, sizeof(dface) * (size_t)fcap);
+                if (!nfaces) { status = -1; break; }
+                faces = nfaces;
+            }
+            static const int fv[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+            for (int f = 0; f < 4; ++f) {
+                dface *F = &faces[nf++];
+                for (int m = 0; m < 3; ++m) F->o[m] = F->v[m] = tt->v[fv[f][m]];
+                /* sort v */
+                for (int a = 1; a < 3; ++a)
+                    for (int b = a; b > 0 && F->v[b] < F->v[b - 1]; --b) {
+                        const int32_t s = F->v[b]; F->v[b] = F->v[b - 1]; F->v[b - 1] = s;
+                    }
+                F->count = 1;
+            }
+        }
+        if (status) break;
+        /* faces met twice are inside the cavity; the others bound it */
+        qsort(faces, (size_t)nf, sizeof(dface), face_cmp);
+        for (int64_t f = 0; f < nf;) {
+            int64_t g = f + 1;
+            while (g < nf && face_cmp(&faces[f], &faces[g]) == 0) ++g;
+            if (g - f == 1) {
+                dtet nt4 = {{faces[f].o[0], faces[f].o[1], faces[f].o[2], (int32_t)ip}};
+                const i128 o = orient3(&pts[nt4.v[0]], &pts[nt4.v[1]], &pts[nt4.v[2]], &pts[nt4.v[3]]);
+                if (o == 0) { status = -2; break; }
+                if (o < 0) { const int32_t s = nt4.v[0]; nt4.v[0] = nt4.v[1]; nt4.v[1] = s; }
+                if (nt == tcap) {
+                    tcap *= 2;
+                    dtet *T2 = (dtet *)realloc(T, sizeof(dtet) * (size_t)tcap);
+                    uint8_t *a2 = (uint8_t *)realloc(alive, (size_t)tcap);
+                    if (T2) T = T2;
+                    if (a2) alive = a2;
+                    if (!T2 || !a2) { status = -1; break; }
+                }
+                T[nt] = nt4;
+                alive[nt] = 1;
+                ++nt;
+            }
+            f = g;
+        }
+        /* compact the list now and then */
+        if (status == 0 && nt > 4 * (n + 4) + 1024) {
+            int64_t w = 0;
+            for (int64_t t = 0; t < nt; ++t)
+                if (alive[t]) { T[w] = T[t]; alive[w] = 1; ++w; }
+            nt = w;
+        }
+    }
+    int64_t out = 0;
+    if (status == 0) {
+        for (int64_t t = 0; t < nt; ++t) {
+            if (!alive[t]) continue;
+            if (T[t].v[0] >= n || T[t].v[1] >= n || T[t].v[2] >= n || T[t].v[3] >= n) continue;
+            if (out >= cap) { status = -1; break; }
+            for (int m = 0; m < 4; ++m) tets[4 * out + m] = (int32_t)ids[T[t].v[m]];
+            ++out;
+        }
+    }
+    free(faces); free(T); free(alive); free(pts); free(ids);
+    return status ? status : out;
 }

@@ -1,0 +1,113 @@
+"""Pins of the oracle's Delaunay reconstruction (Sec. 3.2: a Delaunay
+triangulation over the start locations of the valid basis flows, then
+barycentric interpolation), independent of its code:
+
+* the definition of a Delaunay triangulation, checked directly: the
+  tetrahedra have positive volume, tile the convex hull of the valid points
+  (their volumes add up to the hull volume from scipy's Qhull, and no point
+  of the lattice lies in two interiors), and no valid point lies strictly
+  inside a tetrahedron's circumsphere (floating point, with a tolerance);
+* exactness of barycentric interpolation for affine flow maps;
+* a closed form of the Delaunay property: filling data f(x) = |x|^2 at a
+  missing lattice point j whose two neighbours along some axis are valid
+  gives |j|^2 + 1 exactly (the lower convex hull of the lifted points is the
+  smallest convex combination of |p|^2 over points p averaging to j; all
+  valid points are at least 1 away from j and the pair j +- e_a reaches
+  that bound), which a non-Delaunay triangulation of the same points misses;
+* a full lattice is returned unchanged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _holes(S, frac, seed, balls=0):
+    rng = np.random.default_rng(seed)
+    P = int(np.prod(S))
+    v = rng.random(P) >= frac
+    X = oracle.lattice_coords(S, np.arange(P))
+    for _ in range(balls):
+        c = rng.uniform(2, np.array(S) - 3)
+        r = rng.uniform(1.0, 2.2)
+        v &= np.linalg.norm(X - c, axis=1) > r
+    return v
+
+
+def _vol(V):
+    return np.einsum("ti,ti->t", V[:, 1] - V[:, 0], np.cross(V[:, 2] - V[:, 0], V[:, 3] - V[:, 0])) / 6.0
+
+
+@pytest.mark.parametrize("S,frac,balls,seed", [((7, 6, 5), 0.15, 0, 1), ((9, 8, 7), 0.05, 3, 2), ((6, 6, 6), 0.0, 2, 3)])
+def test_triangulation_is_delaunay_and_tiles_the_hull(S, frac, balls, seed):
+    from scipy.spatial import ConvexHull
+    v = _holes(S, frac, seed, balls)
+    T = oracle.delaunay(S, v)
+    V = oracle.lattice_coords(S, T)
+    vol = _vol(V)
+    assert np.all(vol > 0)
+    pts = oracle.lattice_coords(S, np.flatnonzero(v))
+    assert abs(vol.sum() - ConvexHull(pts).volume) < 1e-9
+    # every vertex is a valid point, every valid point is a vertex
+    assert np.all(v[T.ravel()]) and set(np.unique(T)) == set(np.flatnonzero(v))
+    # empty circumspheres: |p - c|^2 >= r^2 for every valid point p
+    A = 2.0 * (V[:, 1:] - V[:, :1])
+    b = (V[:, 1:] ** 2).sum(-1) - (V[:, :1] ** 2).sum(-1)
+    c = np.linalg.solve(A, b[..., None])[..., 0]
+    r2 = ((V[:, 0] - c) ** 2).sum(-1)
+    d2 = ((pts[None, :, :] - c[:, None, :]) ** 2).sum(-1)
+    assert np.all(d2 >= r2[:, None] - 1e-7)
+    # no lattice point lies strictly inside two tetrahedra
+    grid = oracle.lattice_coords(S, np.arange(int(np.prod(S)))) + 0.123 * np.array([1.0, 0.37, 0.21])
+    Ainv = np.linalg.inv(np.transpose(V[:, 1:] - V[:, :1], (0, 2, 1)))
+    l = np.einsum("tij,ptj->pti", Ainv, grid[:, None, :] - V[None, :, 0, :])
+    inside = np.all(l > 1e-9, axis=2) & (l.sum(axis=2) < 1 - 1e-9)
+    assert inside.sum(axis=1).max() <= 1
+
+
+def test_affine_flow_map_is_reconstructed_exactly():
+    S = (9, 8, 7)
+    v = _holes(S, 0.1, 4, balls=2)
+    M = np.array([[1.1, 0.2, -0.3], [0.05, 0.9, 0.4], [-0.2, 0.1, 1.3]])
+    t = np.array([0.3, -0.7, 1.9])
+    X = oracle.lattice_coords(S, np.arange(int(np.prod(S))))
+    ends = X @ M.T + t
+    f, st = oracle.fill_delaunay(S, np.where(v[:, None], ends, np.nan), v)
+    ok = st > 0
+    assert np.sum(st == 2) > 20
+    assert np.max(np.abs(f[ok] - ends[ok])) < 1e-10
+
+
+def test_quadratic_data_at_holes_with_a_valid_opposite_pair():
+    S = (9, 9, 9)
+    v = _holes(S, 0.12, 5)
+    X = oracle.lattice_coords(S, np.arange(int(np.prod(S))))
+    q = (X ** 2).sum(axis=1, keepdims=True) * np.ones((1, 3))
+    f, st = oracle.fill_delaunay(S, q, v)
+    P = int(np.prod(S))
+    checked = 0
+    for j in np.flatnonzero(~v):
+        x = X[j].astype(int)
+        pairs = []
+        for a in range(3):
+            lo, hi = x.copy(), x.copy()
+            lo[a] -= 1; hi[a] += 1
+            if lo[a] >= 0 and hi[a] < S[a]:
+                il = lo[0] + S[0] * (lo[1] + S[1] * lo[2])
+                ih = hi[0] + S[0] * (hi[1] + S[1] * hi[2])
+                pairs.append(v[il] and v[ih])
+        if any(pairs):
+            assert st[j] == 2
+            assert abs(f[j, 0] - ((X[j] ** 2).sum() + 1.0)) < 1e-9, (j, f[j, 0])
+            checked += 1
+    assert checked > 40
+
+
+def test_full_lattice_unchanged():
+    S = (5, 4, 6)
+    v = np.ones(int(np.prod(S)), dtype=bool)
+    ends = np.random.default_rng(6).standard_normal((int(np.prod(S)), 3))
+    f, st = oracle.fill_delaunay(S, ends, v)
+    assert np.array_equal(f, ends) and np.all(st == 1)
