@@ -429,12 +429,19 @@ def delaunay_interpolate(S, tets: np.ndarray, ends: np.ndarray, q: np.ndarray, t
 def fill_delaunay(S, ends: np.ndarray, valid: np.ndarray):
     """Reconstruction of the missing basis flows of a seed lattice over the
     Delaunay triangulation of the valid ones (Sec. 3.2): each missing entry
-    takes the barycentric interpolant at its own lattice point. Returns
-    (filled ends, status: 1 valid, 2 filled, 0 missing)."""
+    strictly inside the lattice takes the barycentric interpolant at its own
+    lattice point; entries on the lattice's boundary faces stay missing.
+    Returns (filled ends, status: 1 valid, 2 filled, 0 missing)."""
     v = np.asarray(valid).reshape(-1).astype(bool)
     E = np.asarray(ends, dtype=np.float64).reshape(-1, 3).copy()
     status = np.where(v, 1, 0).astype(np.uint8)
-    miss = np.flatnonzero(~v)
+    # entries on the lattice's boundary faces (neighbours on one side only)
+    # stay missing (reading)
+    X = lattice_coords(S, np.arange(v.size))
+    hi = np.asarray([int(a) for a in S], dtype=np.float64) - 1
+    interior = np.all((X > 0) & (X < hi), axis=1)
+    E[~v & ~interior] = np.nan
+    miss = np.flatnonzero(~v & interior)
     if miss.size and v.sum() >= 4:
         tets = delaunay(S, v)
         vals, found = delaunay_interpolate(S, tets, E, lattice_coords(S, miss))
