@@ -298,6 +298,23 @@ BTO_API bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_end
                                     const uint8_t *d_valid, float *d_out, uint8_t *d_status,
                                     bto_stream stream);
 
+/* Reconstruction over a Delaunay triangulation (Sec. 3.2: a Delaunay
+ * triangulation over the start locations of the valid basis flows of the
+ * own and adjacent blocks, then barycentric interpolation). Same lattice,
+ * arguments and outputs as bto_fill_lattice: a missing entry takes the
+ * barycentric interpolant of the end positions at the vertices of the
+ * Delaunay tetrahedron of the valid lattice points that holds its own
+ * lattice point. Ties among cospherical lattice points are broken by
+ * infinitesimal lifted weights ordered by canonical lattice id. Each
+ * missing entry is solved over the valid points within 2 to 6 lattice
+ * units of it (the smallest window that holds its tetrahedron's
+ * circumsphere); an entry on the lattice's boundary faces (neighbours on
+ * one side only), outside the hull of the valid points, or whose
+ * tetrahedron needs a larger window, stays missing (NaN, status 0). */
+BTO_API bto_status bto_fill_delaunay(const int32_t lattice[3], const float *d_ends,
+                                     const uint8_t *d_valid, float *d_out, uint8_t *d_status,
+                                     bto_stream stream);
+
 /* Pathline stitching (Sec. 3.2): new particles follow the basis flows of
  * successive intervals. In interval k a particle's next position is the
  * trilinear interpolant (Eq. 1 per axis; bto_stitch_pathlines_ex also

@@ -85,6 +85,7 @@ def _declare(lib):
         "bto_check_bounds_build": ([], ctypes.c_int32),
         "bto_bounds_failures": ([c_u64p, ctypes.c_int32], ctypes.c_int),
         "bto_fill_lattice": ([c_i32p, vp, vp, vp, vp, vp], ctypes.c_int),
+        "bto_fill_delaunay": ([c_i32p, vp, vp, vp, vp, vp], ctypes.c_int),
         "bto_stitch_pathlines": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp],
                                  ctypes.c_int),
         "bto_stitch_pathlines_ex": ([c_i32p, c_fp, c_fp, ctypes.c_int32, vp, ctypes.c_int64, vp, vp,
@@ -321,6 +322,11 @@ def bto_bounds_failures(reset: bool = False) -> int:
 def bto_fill_lattice(lattice, d_ends, d_valid, d_out, d_status=None, stream=None) -> None:
     _check(load().bto_fill_lattice(_arr(ctypes.c_int32, lattice), _addr(d_ends), _addr(d_valid), _addr(d_out),
                                    _addr(d_status), _stream(stream)), "bto_fill_lattice")
+
+
+def bto_fill_delaunay(lattice, d_ends, d_valid, d_out, d_status=None, stream=None) -> None:
+    _check(load().bto_fill_delaunay(_arr(ctypes.c_int32, lattice), _addr(d_ends), _addr(d_valid), _addr(d_out),
+                                    _addr(d_status), _stream(stream)), "bto_fill_delaunay")
 
 
 def bto_stitch_pathlines(lattice, origin, spacing, intervals: int, d_ends_table, nq: int, d_start, d_path,

@@ -1039,6 +1039,22 @@ bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_ends, const
     return BTO_OK;
 }
 
+bto_status bto_fill_delaunay(const int32_t lattice[3], const float *d_ends, const uint8_t *d_valid, float *d_out,
+                             uint8_t *d_status, bto_stream stream) {
+    if (!lattice || !d_ends || !d_valid || !d_out) return BTO_ERR_INVALID_ARG;
+    if (lattice[0] < 1 || lattice[1] < 1 || lattice[2] < 1) return BTO_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_ends) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
+        return BTO_ERR_INVALID_ARG;
+    const int64_t P = (int64_t)lattice[0] * lattice[1] * lattice[2];
+    if (P > (1ll << 31) - 1) return BTO_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    BTO_CUDA(cudaGetDevice(&dev));
+    BTO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((P + 127) / 128, (int64_t)sms * 16));
+    BTO_CUDA(bto::launch_fill_delaunay(lattice, d_ends, d_valid, d_out, d_status, grid, (cudaStream_t)stream));
+    return BTO_OK;
+}
+
 bto_status bto_stitch_pathlines(const int32_t lattice[3], const float origin[3], const float spacing[3],
                                 int32_t intervals, const float *const *d_ends_table, int64_t nq,
                                 const float *d_start, float *d_path, bto_stream stream) {
@@ -1085,8 +1101,9 @@ int32_t bto_check_bounds_build(void) {
 
 bto_status bto_bounds_failures(uint64_t *count, int32_t reset) {
     if (!count) return BTO_ERR_INVALID_ARG;
-    const unsigned long long parts[3] = {bto::bounds_failures_kernels(reset != 0), bto::bounds_failures_tiled(reset != 0),
-                                         bto::bounds_failures_posthoc(reset != 0)};
+    const unsigned long long parts[4] = {bto::bounds_failures_kernels(reset != 0), bto::bounds_failures_tiled(reset != 0),
+                                         bto::bounds_failures_posthoc(reset != 0),
+                                         bto::bounds_failures_delaunay(reset != 0)};
     uint64_t total = 0;
     for (const unsigned long long v : parts) {
         if (v == ~0ull) {

@@ -80,6 +80,7 @@ __device__ __forceinline__ bool in_bounds_check(bool ok, int32_t *err) {
 unsigned long long bounds_failures_kernels(bool reset);
 unsigned long long bounds_failures_tiled(bool reset);
 unsigned long long bounds_failures_posthoc(bool reset);
+unsigned long long bounds_failures_delaunay(bool reset);
 
 // One block of the uniform grid, as the kernels see it. Positions inside the
 // library are block-local CELL coordinates xi = (x - origin) / h, so node i
@@ -256,6 +257,8 @@ cudaError_t launch_ingest(const void *field, const void *const *fields, int b, i
 cudaError_t launch_stitch(const int32_t S[3], const float origin[3], const float spacing[3], int32_t intervals,
                           const float *const *ends_table, int64_t nq, const float *start, float *path, int grid,
                           cudaStream_t s, bool barycentric);
+cudaError_t launch_fill_delaunay(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
+                                 uint8_t *status, int grid, cudaStream_t s);
 cudaError_t launch_fill_lattice(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
                                 uint8_t *status, int grid, cudaStream_t s);
 cudaError_t launch_write_term(const BlockDev *blocks, int32_t nb, int64_t P, float4 *term,

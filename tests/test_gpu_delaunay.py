@@ -1,0 +1,104 @@
+"""GPU Delaunay reconstruction (bto_fill_delaunay) against the FP64 oracle's
+Bowyer-Watson triangulation (oracle.fill_delaunay), through the C ABI.
+
+Both sides decide with exact integer predicates under the same tie-breaking
+reading, so they pick the same Delaunay tetrahedron (or, for a point on a
+shared face, tetrahedra whose barycentric interpolants agree there): the
+statuses must be identical and the filled ends agree to FP32 rounding of
+the FP64 result (relative 1e-6 of the ends' scale).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_02003_gb300 import bto
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    from paper_2004_02003_gb300 import build
+    build.build()
+    bto.load()
+
+
+def _holes(S, frac, seed, balls=0):
+    rng = np.random.default_rng(seed)
+    P = int(np.prod(S))
+    v = rng.random(P) >= frac
+    X = oracle.lattice_coords(S, np.arange(P))
+    for _ in range(balls):
+        c = rng.uniform(1, np.array(S) - 2)
+        r = rng.uniform(1.0, 2.5)
+        v &= np.linalg.norm(X - c, axis=1) > r
+    return v
+
+
+def _gpu_fill(S, ends, valid):
+    import torch
+    e = torch.from_numpy(np.ascontiguousarray(ends, dtype=np.float32)).cuda()
+    v = torch.from_numpy(np.ascontiguousarray(valid, dtype=np.uint8)).cuda()
+    out = torch.empty_like(e)
+    st = torch.empty_like(v)
+    bto.bto_fill_delaunay(S, e, v, out, st)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), st.cpu().numpy()
+
+
+@pytest.mark.parametrize("S,frac,balls,seed", [((12, 11, 10), 0.08, 3, 11), ((9, 14, 8), 0.2, 0, 12),
+                                              ((10, 10, 10), 0.02, 5, 13), ((6, 5, 4), 0.3, 1, 14)])
+def test_delaunay_fill_matches_oracle(S, frac, balls, seed):
+    v = _holes(S, frac, seed, balls)
+    X = oracle.lattice_coords(S, np.arange(int(np.prod(S))))
+    ends = np.stack([X[:, 0] + 0.3 * np.sin(0.7 * X[:, 1]), X[:, 1] + 0.2 * np.cos(0.5 * X[:, 2] + X[:, 0]),
+                     X[:, 2] + 0.1 * X[:, 0] * X[:, 1] / 10.0], axis=1)
+    ends_in = np.where(v[:, None], ends, np.nan).astype(np.float32)
+    ref, st_o = oracle.fill_delaunay(S, ends_in.astype(np.float64), v)
+    got, st_g = _gpu_fill(S, ends_in, v)
+    bad = np.flatnonzero(st_g != st_o)
+    if bad.size:
+        P = np.flatnonzero(v)
+        for j in bad[:12]:
+            d = np.sqrt(((oracle.lattice_coords(S, P) - X[j]) ** 2).sum(axis=1)).min()
+            print("mismatch at", X[j], "gpu", st_g[j], "oracle", st_o[j], "nearest valid %.2f" % d)
+    assert bad.size == 0, f"{bad.size} statuses differ"
+    filled = st_o == 2
+    assert filled.sum() > 0
+    scale = np.abs(ref[filled]).max()
+    assert np.max(np.abs(got[filled] - ref[filled])) <= 2e-6 * scale
+    assert np.array_equal(got[st_o == 1], ends_in[st_o == 1])
+    assert np.all(np.isnan(got[st_o == 0]))
+
+
+def test_delaunay_fill_affine_and_quadratic_closed_forms():
+    S = (16, 15, 14)
+    v = _holes(S, 0.06, 21, balls=4)
+    X = oracle.lattice_coords(S, np.arange(int(np.prod(S))))
+    M = np.array([[1.1, 0.2, -0.3], [0.05, 0.9, 0.4], [-0.2, 0.1, 1.3]])
+    aff = (X @ M.T + np.array([0.5, -1.0, 2.0])).astype(np.float32)
+    got, st = _gpu_fill(S, np.where(v[:, None], aff, np.nan), v)
+    ok = st == 2
+    assert ok.sum() > 50
+    assert np.max(np.abs(got[ok] - aff[ok])) < 1e-4
+    # |x|^2 at holes with a valid opposite neighbour pair: |j|^2 + 1 exactly
+    q = ((X ** 2).sum(axis=1, keepdims=True) * np.ones((1, 3))).astype(np.float32)
+    gq, sq = _gpu_fill(S, np.where(v[:, None], q, np.nan), v)
+    n = 0
+    for j in np.flatnonzero(~v):
+        x = X[j].astype(int)
+        if np.any(x == 0) or np.any(x == np.array(S) - 1):
+            assert sq[j] == 0            # boundary faces stay missing
+            continue
+        for a in range(3):
+            lo, hi = x.copy(), x.copy()
+            lo[a] -= 1; hi[a] += 1
+            if lo[a] < 0 or hi[a] >= S[a]:
+                continue
+            il = lo[0] + S[0] * (lo[1] + S[1] * lo[2])
+            ih = hi[0] + S[0] * (hi[1] + S[1] * hi[2])
+            if v[il] and v[ih]:
+                assert sq[j] == 2 and gq[j, 0] == np.float32((X[j] ** 2).sum() + 1.0), j
+                n += 1
+                break
+    assert n > 50
