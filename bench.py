@@ -538,9 +538,12 @@ def summary(res):
                 return None
             d = d[k]
         return round(d, 4) if isinstance(d, float) and abs(d) < 10 else d
+    iv = (res.get("large") or {}).get("intervals") or [{}]
     return {"value": get("value"), "frac": get("roofline", "frac"), "graph": get("graph_value"),
             "batched_value": get("batched", "batched_value"), "batched_frac": get("batched", "roofline", "frac"),
             "large_value": get("large", "batched_value"), "large_frac": get("large", "roofline", "frac"),
+            "large_accuracy_percent_lattice_delaunay": [iv[0].get("accuracy_percent"),
+                                                        (iv[0].get("delaunay") or {}).get("accuracy_percent")],
             "adjoint_fwd_bwd_vs_plain": get("adjoint", "forward_backward_vs_plain"),
             "e2e": get("e2e", "value")}
 
@@ -1059,6 +1062,12 @@ def large_leg(args, dev, stream):
         l2, mx = err.mean().item(), err.max().item()
         filled_sets.append(filled)
         global_sets.append(gout["ends"].clone())
+        # the paper's own reconstruction: Delaunay triangulation of the valid
+        # basis flows of all blocks, barycentric interpolation (Sec. 3.2);
+        # first interval only (a post hoc step of seconds)
+        delaunay = None
+        if k == 0:
+            delaunay = delaunay_fill_report(bto, G, h, lat_e, lat_v, gout, filled, status, ok, stream)
         del lat_e, lat_v
         report.append({"interval": k, "terminated_frac_bto": float(1 - bv.float().mean().item()),
                        "terminated_frac_global": float(1 - (gout["valid"] == 1).float().mean().item()),
@@ -1067,7 +1076,8 @@ def large_leg(args, dev, stream):
                        "valid_end_deviation_cells_p50_p99_p9999": q,
                        "still_missing_after_fill": int((status == 0).sum().item()),
                        "total_average_l2": l2, "max_l2": mx,
-                       "accuracy_percent": (h - l2) / h * 100.0})
+                       "accuracy_percent": (h - l2) / h * 100.0,
+                       **({"delaunay": delaunay} if delaunay else {})})
     tape.close()
     del act
     for p in plain:
@@ -1118,6 +1128,32 @@ def large_leg(args, dev, stream):
             "intervals": report,
             "greatest_max_l2": max(maxes), "average_max_l2": float(np.mean(maxes)),
             "pathlines_vs_rk4_ground_truth": path_err}
+
+
+def delaunay_fill_report(bto, G, h, lat_e, lat_v, gout, filled, status, ok, stream):
+    """The Delaunay reconstruction (bto_fill_delaunay) of one interval's
+    global seed lattice, its accuracy against the global map (Sec. 4.3) and
+    its time, beside the lattice fill's on the entries both fill."""
+    import torch
+    dfill = torch.empty_like(lat_e)
+    dstat = torch.empty_like(lat_v)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    bto.bto_fill_delaunay((G, G, G), lat_e, lat_v, dfill, dstat)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    okd = (gout["valid"] == 1) & (dstat > 0)
+    errd = (dfill[okd].double() - gout["ends"][okd].double()).norm(dim=1)
+    l2d, mxd = errd.mean().item(), errd.max().item()
+    both_f = okd & ok & (status == 2) & (dstat == 2)
+    el = (filled[both_f].double() - gout["ends"][both_f].double()).norm(dim=1)
+    ed = (dfill[both_f].double() - gout["ends"][both_f].double()).norm(dim=1)
+    return {"total_average_l2": l2d, "max_l2": mxd, "accuracy_percent": (h - l2d) / h * 100.0,
+            "still_missing_after_fill": int((dstat == 0).sum().item()), "filled": int((dstat == 2).sum().item()),
+            "fill_ms": d0.elapsed_time(d1),
+            "filled_by_both": int(both_f.sum().item()),
+            "mean_l2_on_entries_both_fill_lattice_delaunay": [el.mean().item(), ed.mean().item()],
+            "max_l2_on_entries_both_fill_lattice_delaunay": [el.max().item(), ed.max().item()]}
 
 
 def e2e(args, ctx, fields, dt, dev, stream, nb, world=1):
