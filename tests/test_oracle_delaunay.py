@@ -14,7 +14,11 @@ barycentric interpolation), independent of its code:
   smallest convex combination of |p|^2 over points p averaging to j; all
   valid points are at least 1 away from j and the pair j +- e_a reaches
   that bound), which a non-Delaunay triangulation of the same points misses;
-* a full lattice is returned unchanged.
+* a full lattice is returned unchanged;
+* the tie-breaking reading: on small lattices, full and with holes, the
+  tetrahedra equal those of a brute-force lower convex hull of the points
+  lifted with explicit exact rational weights (a linear solve per 4-point
+  set and a test against every other point, no determinant).
 """
 import numpy as np
 import pytest
@@ -114,3 +118,59 @@ def test_full_lattice_unchanged():
     ends = np.random.default_rng(6).standard_normal((int(np.prod(S)), 3))
     f, st = oracle.fill_delaunay(S, ends, v)
     assert np.array_equal(f, ends) and np.all(st == 1)
+
+
+def _regular_triangulation_brute_force(S, valid, t):
+    """Lower convex hull of the valid lattice points lifted to
+    w(j) = |j|^2 + t^(r + 1), r = the canonical lattice id, in exact
+    rational arithmetic: a 4-point set is a tetrahedron of the regular
+    triangulation when the affine function through its four lifted points
+    lies strictly below every other lifted point. With t = 1e-6 the explicit
+    weights order ties as the reading's infinitesimals do on a lattice this
+    small (every cofactor is an integer below 100 in size, so a weight
+    outweighs all later ones together, and all of them together stay below
+    the unit step of an unperturbed determinant)."""
+    from fractions import Fraction
+    from itertools import combinations
+    ids = [int(i) for i in np.flatnonzero(valid)]
+    X = {i: [int(c) for c in oracle.lattice_coords(S, np.array([i]))[0]] for i in ids}
+    w = {i: Fraction(sum(c * c for c in X[i])) + t ** (i + 1) for i in ids}
+
+    def solve(rows, rhs):
+        # Gauss-Jordan elimination over the rationals; None when singular
+        m = [[Fraction(v) for v in r] + [rhs[k]] for k, r in enumerate(rows)]
+        n = len(m)
+        for c in range(n):
+            piv = next((r for r in range(c, n) if m[r][c] != 0), None)
+            if piv is None:
+                return None
+            m[c], m[piv] = m[piv], m[c]
+            for r in range(n):
+                if r != c and m[r][c] != 0:
+                    f = m[r][c] / m[c][c]
+                    m[r] = [a - f * b for a, b in zip(m[r], m[c])]
+        return [m[r][n] / m[r][r] for r in range(n)]
+
+    tets = set()
+    for q in combinations(ids, 4):
+        coef = solve([X[i] + [1] for i in q], [w[i] for i in q])
+        if coef is None:          # coplanar points span no tetrahedron
+            continue
+        if all(w[e] > sum(a * b for a, b in zip(coef, X[e] + [1])) for e in ids if e not in q):
+            tets.add(tuple(sorted(q)))
+    return tets
+
+
+@pytest.mark.parametrize("S,holes", [((3, 3, 2), []), ((3, 3, 3), [13]), ((3, 3, 3), [7, 13, 15]),
+                                     ((4, 3, 2), [5, 18]), ((2, 2, 2), [])])
+def test_tie_breaking_matches_the_lower_hull_with_exact_weights(S, holes):
+    """Lattice points are cospherical in eights, so only the tie-breaking
+    reading fixes the triangulation. The oracle's must be the brute-force
+    lower hull of the lifted points with explicit weights ordered as the
+    reading orders its infinitesimals (lowest canonical id largest)."""
+    from fractions import Fraction
+    v = np.ones(int(np.prod(S)), dtype=bool)
+    v[holes] = False
+    want = _regular_triangulation_brute_force(S, v, Fraction(1, 10 ** 6))
+    got = {tuple(sorted(int(i) for i in t)) for t in oracle.delaunay(S, v)}
+    assert got == want
