@@ -1148,8 +1148,19 @@ def delaunay_fill_report(bto, G, h, lat_e, lat_v, gout, filled, status, ok, stre
     both_f = okd & ok & (status == 2) & (dstat == 2)
     el = (filled[both_f].double() - gout["ends"][both_f].double()).norm(dim=1)
     ed = (dfill[both_f].double() - gout["ends"][both_f].double()).norm(dim=1)
+    # where the entries left missing lie: on the lattice's boundary faces,
+    # and how many of them the global map keeps valid (lattice fill, Delaunay)
+    j = torch.arange(G ** 3, device=dstat.device, dtype=torch.int32)
+    jx, jy, jz = j % G, (j // G) % G, j // (G * G)
+    face = (jx == 0) | (jx == G - 1) | (jy == 0) | (jy == G - 1) | (jz == 0) | (jz == G - 1)
+    del j, jx, jy, jz
+    gval = gout["valid"] == 1
+    miss_d = dstat == 0
     return {"total_average_l2": l2d, "max_l2": mxd, "accuracy_percent": (h - l2d) / h * 100.0,
-            "still_missing_after_fill": int((dstat == 0).sum().item()), "filled": int((dstat == 2).sum().item()),
+            "still_missing_after_fill": int(miss_d.sum().item()), "filled": int((dstat == 2).sum().item()),
+            "still_missing_on_boundary_faces": int((miss_d & face).sum().item()),
+            "still_missing_valid_in_global_map_lattice_delaunay": [int(((status == 0) & gval).sum().item()),
+                                                                   int((miss_d & gval).sum().item())],
             "fill_ms": d0.elapsed_time(d1),
             "filled_by_both": int(both_f.sum().item()),
             "mean_l2_on_entries_both_fill_lattice_delaunay": [el.mean().item(), ed.mean().item()],
