@@ -429,26 +429,23 @@ def delaunay_interpolate(S, tets: np.ndarray, ends: np.ndarray, q: np.ndarray, t
 def fill_delaunay(S, ends: np.ndarray, valid: np.ndarray):
     """Reconstruction of the missing basis flows of a seed lattice over the
     Delaunay triangulation of the valid ones (Sec. 3.2): each missing entry
-    strictly inside the lattice takes the barycentric interpolant at its own
-    lattice point; entries on the lattice's boundary faces stay missing.
+    takes the barycentric interpolant at its own lattice point over the
+    tetrahedron that holds it. An entry on the lattice's boundary faces lies
+    on a face of that tetrahedron (its weight on the vertex off the face is
+    zero); an entry outside the hull of the valid points stays missing. A
+    lattice one point thick along some axis has no tetrahedra, and its
+    missing entries stay missing.
     Returns (filled ends, status: 1 valid, 2 filled, 0 missing)."""
     v = np.asarray(valid).reshape(-1).astype(bool)
     E = np.asarray(ends, dtype=np.float64).reshape(-1, 3).copy()
     status = np.where(v, 1, 0).astype(np.uint8)
-    # entries on the lattice's boundary faces (neighbours on one side only)
-    # stay missing (reading)
-    X = lattice_coords(S, np.arange(v.size))
-    hi = np.asarray([int(a) for a in S], dtype=np.float64) - 1
-    interior = np.all((X > 0) & (X < hi), axis=1)
-    E[~v & ~interior] = np.nan
-    miss = np.flatnonzero(~v & interior)
-    if miss.size and v.sum() >= 4:
+    miss = np.flatnonzero(~v)
+    E[miss] = np.nan
+    if miss.size and v.sum() >= 4 and min(int(a) for a in S) > 1:
         tets = delaunay(S, v)
         vals, found = delaunay_interpolate(S, tets, E, lattice_coords(S, miss))
         E[miss] = vals
         status[miss[found]] = 2
-    else:
-        E[miss] = np.nan
     return E, status
 
 

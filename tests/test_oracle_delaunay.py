@@ -9,11 +9,15 @@ barycentric interpolation), independent of its code:
   inside a tetrahedron's circumsphere (floating point, with a tolerance);
 * exactness of barycentric interpolation for affine flow maps;
 * a closed form of the Delaunay property: filling data f(x) = |x|^2 at a
-  missing interior lattice point j whose two neighbours along some axis are valid
+  missing lattice point j whose two neighbours along some axis are valid
   gives |j|^2 + 1 exactly (the lower convex hull of the lifted points is the
   smallest convex combination of |p|^2 over points p averaging to j; all
   valid points are at least 1 away from j and the pair j +- e_a reaches
   that bound), which a non-Delaunay triangulation of the same points misses;
+* on the lattice's edges, the linear interpolant of the nearest valid
+  neighbours along the edge (both bounding planes support the hull); a
+  missing corner, or an edge entry with no valid neighbour on one side,
+  stays missing; affine maps filled exactly on faces;
 * a full lattice is returned unchanged;
 * the tie-breaking reading: on small lattices, full and with holes, the
   tetrahedra equal those of a brute-force lower convex hull of the points
@@ -94,9 +98,6 @@ def test_quadratic_data_at_holes_with_a_valid_opposite_pair():
     checked = 0
     for j in np.flatnonzero(~v):
         x = X[j].astype(int)
-        if np.any(x == 0) or np.any(x == np.array(S) - 1):
-            assert st[j] == 0            # boundary faces stay missing
-            continue
         pairs = []
         for a in range(3):
             lo, hi = x.copy(), x.copy()
@@ -110,6 +111,59 @@ def test_quadratic_data_at_holes_with_a_valid_opposite_pair():
             assert abs(f[j, 0] - ((X[j] ** 2).sum() + 1.0)) < 1e-9, (j, f[j, 0])
             checked += 1
     assert checked > 40
+
+
+def test_boundary_edges_faces_and_corners():
+    """On a lattice edge (two coordinates at the lattice's bounds) both
+    bounding planes support the hull of the valid points, so the tetrahedron
+    holding a missing entry meets the edge line in the segment between its
+    nearest valid neighbours along the edge: the entry takes their linear
+    interpolant, whatever the data. On a face an affine map is still filled
+    exactly, a missing corner lies outside the hull and stays missing, and
+    an edge entry with no valid neighbour on one side stays missing."""
+    S = (9, 8, 7)
+    rng = np.random.default_rng(12)
+    P = int(np.prod(S))
+    X = oracle.lattice_coords(S, np.arange(P)).astype(int)
+    v = rng.random(P) >= 0.3
+    ends = rng.standard_normal((P, 3))
+    f, st = oracle.fill_delaunay(S, np.where(v[:, None], ends, np.nan), v)
+    hi = np.array(S) - 1
+    n_edge = 0
+    for j in np.flatnonzero(~v):
+        fixed = (X[j] == 0) | (X[j] == hi)
+        if fixed.sum() == 3:
+            assert st[j] == 0
+        if fixed.sum() != 2:
+            continue
+        a = int(np.flatnonzero(~fixed)[0])
+        line = [k for k in range(P) if np.all(np.delete(X[k], a) == np.delete(X[j], a)) and v[k]]
+        below = [k for k in line if X[k][a] < X[j][a]]
+        above = [k for k in line if X[k][a] > X[j][a]]
+        if not below or not above:
+            assert st[j] == 0
+            continue
+        lo = max(below, key=lambda k: X[k][a])
+        up = min(above, key=lambda k: X[k][a])
+        t = (X[j][a] - X[lo][a]) / (X[up][a] - X[lo][a])
+        assert st[j] == 2
+        assert np.max(np.abs(f[j] - ((1 - t) * ends[lo] + t * ends[up]))) < 1e-12
+        n_edge += 1
+    assert n_edge > 10
+    # an affine map is filled exactly on faces too
+    M = np.array([[0.7, -0.2, 0.1], [0.3, 1.2, -0.4], [0.05, 0.1, 0.9]])
+    aff = X @ M.T + np.array([1.0, 2.0, -3.0])
+    f, st = oracle.fill_delaunay(S, np.where(v[:, None], aff, np.nan), v)
+    face = np.any((X == 0) | (X == hi), axis=1)
+    assert np.sum((st == 2) & face) > 20
+    assert np.max(np.abs(f[st > 0] - aff[st > 0])) < 1e-10
+
+
+def test_flat_lattice_has_no_tetrahedra():
+    S = (6, 5, 1)
+    v = np.random.default_rng(13).random(30) >= 0.2
+    f, st = oracle.fill_delaunay(S, np.zeros((30, 3)), v)
+    assert np.all(st[~v] == 0) and np.all(np.isnan(f[~v])) and np.all(st[v] == 1)
 
 
 def test_full_lattice_unchanged():
