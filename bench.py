@@ -1161,6 +1161,7 @@ def delaunay_fill_report(bto, G, h, lat_e, lat_v, gout, filled, status, ok, stre
             "still_missing_on_boundary_faces": int((miss_d & face).sum().item()),
             "still_missing_valid_in_global_map_lattice_delaunay": [int(((status == 0) & gval).sum().item()),
                                                                    int((miss_d & gval).sum().item())],
+            "still_missing_valid_in_global_map_on_boundary_faces": int((miss_d & gval & face).sum().item()),
             "fill_ms": d0.elapsed_time(d1),
             "filled_by_both": int(both_f.sum().item()),
             "mean_l2_on_entries_both_fill_lattice_delaunay": [el.mean().item(), ed.mean().item()],

@@ -307,10 +307,15 @@ BTO_API bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_end
  * lattice point. Ties among cospherical lattice points are broken by
  * infinitesimal lifted weights ordered by canonical lattice id. Each
  * missing entry is solved over the valid points within 2 to 6 lattice
- * units of it (the smallest window that holds its tetrahedron's
- * circumsphere); an entry on the lattice's boundary faces (neighbours on
- * one side only), outside the hull of the valid points, or whose
- * tetrahedron needs a larger window, stays missing (NaN, status 0). */
+ * units of it, 2 to 12 on a boundary face (the smallest window that
+ * holds its simplex's circumsphere). An entry on a boundary face of the
+ * lattice lies on the hull of the valid points and takes the interpolant
+ * over the face's triangle (the tetrahedra meet the face in the Delaunay
+ * triangulation of the face's own points); one on a boundary edge takes
+ * the linear interpolant of its nearest valid neighbours along the edge. A
+ * corner, an entry outside the hull of the valid points, one whose
+ * tetrahedron (triangle) needs a larger window, and every missing entry of
+ * a lattice one point thick along some axis stay missing (NaN, status 0). */
 BTO_API bto_status bto_fill_delaunay(const int32_t lattice[3], const float *d_ends,
                                      const uint8_t *d_valid, float *d_out, uint8_t *d_status,
                                      bto_stream stream);

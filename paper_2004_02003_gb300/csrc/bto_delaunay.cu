@@ -21,6 +21,18 @@
 // (no lattice point outside the window can then lie inside it); otherwise
 // the window grows (radius 2 to 6 lattice units) and the walk restarts.
 //
+// Entries on the lattice's outer faces lie on the hull of the valid points.
+// There the face's plane supports the lifted point set, so the tetrahedra
+// meet the face in the regular triangulation of the face's own points
+// under the same weights (|j|^2 differs from the face's squared in-plane
+// coordinates by a constant): such an entry is solved by the same simplex
+// method in the face's two free coordinates, with triangles. On a lattice
+// edge two planes support the hull, and the triangulation meets the edge
+// line in the segments between consecutive valid points: the entry takes
+// the linear interpolant of its nearest valid neighbours along the edge. A
+// missing corner is outside the hull. A lattice one point thick along an
+// axis has no tetrahedra; its missing entries stay missing.
+//
 // Cospherical lattice points (a cell's 8 corners) make the Delaunay
 // triangulation non-unique. Ties are broken as if the lifted weights were
 // |j|^2 + d_r(j), with infinitesimals d_0 >> d_1 >> ... > 0 ordered by the
@@ -124,6 +136,11 @@ __device__ __forceinline__ int64_t lattice_rank(int3 S, int64_t x, int64_t y, in
 constexpr int64_t kFar = 1024;   // distance of the four starting points, lattice units
 constexpr int kMaxPivots = 512;
 constexpr int kMaxWindow = 6;      // largest window radius, lattice units
+constexpr int kMaxWindow2 = 12;    // on a face (a window of 25 x 25 points)
+// Largest lattice (face) scanned whole to show that a facet (edge) through
+// the query point bounds the hull of all valid points.
+constexpr int64_t kHullScan3 = (int64_t)1 << 21;
+constexpr int64_t kHullScan2 = (int64_t)1 << 20;
 
 // Outcome of one walk in a window of radius R around the lattice point c:
 // 1 and the tetrahedron with q's barycentric coordinates, or 0 (no result
@@ -168,6 +185,98 @@ __device__ void start_tetrahedron(int64_t P, LPt (&T)[4]) {
     if (orient(T[0], T[1], T[2], T[3]) < 0) { const LPt s = T[0]; T[0] = T[1]; T[1] = s; }
 }
 
+// True when the circumsphere of T, centred at ctr (relative to the query
+// point c) with squared radius r2, stays clear of every lattice plane just
+// outside the window [x0, x1] x [y0, y1] x [z0, z1] that lies inside the
+// lattice: then no lattice point outside the window is inside it.
+__device__ bool sphere_fits(const double (&ctr)[3], double r2, int3 S, int64_t cx, int64_t cy, int64_t cz,
+                            int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0, int64_t z1) {
+    const double rad = sqrt(r2) * (1.0 + 1e-12) + 1e-9;
+    const double lo[3] = {(double)(x0 - cx), (double)(y0 - cy), (double)(z0 - cz)};
+    const double hi[3] = {(double)(x1 - cx), (double)(y1 - cy), (double)(z1 - cz)};
+    const int64_t ext[3] = {S.x, S.y, S.z};
+    const int64_t cc[3] = {cx, cy, cz};
+    for (int m = 0; m < 3; ++m) {
+        // a window edge on the lattice boundary needs no margin
+        if (cc[m] + (int64_t)lo[m] > 0 && ctr[m] - rad <= lo[m] - 1.0) return false;
+        if (cc[m] + (int64_t)hi[m] < ext[m] - 1 && ctr[m] + rad >= hi[m] + 1.0) return false;
+    }
+    return true;
+}
+
+// The walk ended with one starting point (vertex kf of T) at weight exactly
+// 0: q lies on the facet F of the other three vertices, and no window point
+// is inside the sphere through F and the far starting point. F is a facet
+// of the Delaunay triangulation of all valid points, and q's interpolant is
+// the one over F, when (a) wrapping across F to the valid window point D on
+// the other side whose sphere through F holds no other such point gives a
+// tetrahedron whose sphere holds no valid window point at all and fits in
+// the window, or (b) no valid point of the lattice lies strictly on the far
+// side of F (F is then on the hull). Either way T[kf] is replaced by a
+// valid point (D, or a vertex of F) with weight 0.
+__device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz,
+                             int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0, int64_t z1, LPt (&T)[4],
+                             int kf) {
+    const int64_t o = orient(T[0], T[1], T[2], T[3]);
+    bool far_pt = false, have = false;
+    LPt D = T[(kf + 1) & 3];
+    for (int64_t z = z0; z <= z1; ++z)
+        for (int64_t y = y0; y <= y1; ++y)
+            for (int64_t x = x0; x <= x1; ++x) {
+                const int64_t r = lattice_rank(S, x, y, z);
+                if (!valid[r] || T[0].rank == r || T[1].rank == r || T[2].rank == r || T[3].rank == r) continue;
+                const LPt p = {x - cx, y - cy, z - cz, r};
+                LPt u[4] = {T[0], T[1], T[2], T[3]};
+                u[kf] = p;
+                const int64_t so = orient(u[0], u[1], u[2], u[3]);
+                if (so == 0) continue;
+                if ((so > 0) == (o > 0)) { far_pt = true; continue; }
+                if (!have) { D = p; have = true; continue; }
+                LPt t4[4] = {T[0], T[1], T[2], T[3]};
+                t4[kf] = D;
+                if (orient(t4[0], t4[1], t4[2], t4[3]) < 0) { const LPt sw = t4[0]; t4[0] = t4[1]; t4[1] = sw; }
+                if (lifted_sign(t4, p) < 0) D = p;
+            }
+    if (have) {
+        LPt t4[4] = {T[0], T[1], T[2], T[3]};
+        t4[kf] = D;
+        if (orient(t4[0], t4[1], t4[2], t4[3]) < 0) { const LPt sw = t4[0]; t4[0] = t4[1]; t4[1] = sw; }
+        bool empty = true;
+        for (int64_t z = z0; z <= z1 && empty; ++z)
+            for (int64_t y = y0; y <= y1 && empty; ++y)
+                for (int64_t x = x0; x <= x1 && empty; ++x) {
+                    const int64_t r = lattice_rank(S, x, y, z);
+                    if (!valid[r] || t4[0].rank == r || t4[1].rank == r || t4[2].rank == r || t4[3].rank == r) continue;
+                    const LPt p = {x - cx, y - cy, z - cz, r};
+                    if (lifted_sign(t4, p) < 0) empty = false;
+                }
+        double ctr[3], r2;
+        circumsphere(t4, ctr, r2);
+        if (empty && sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1)) {
+            T[kf] = D;
+            return true;
+        }
+    }
+    // (b): no valid point of the lattice strictly on the far side of F (a
+    // whole-lattice scan, for lattices of up to kHullScan3 points)
+    if (!far_pt && (int64_t)S.x * S.y * S.z <= kHullScan3) {
+        for (int64_t z = 0; z < S.z; ++z)
+            for (int64_t y = 0; y < S.y; ++y)
+                for (int64_t x = 0; x < S.x; ++x) {
+                    const int64_t r = lattice_rank(S, x, y, z);
+                    if (!valid[r]) continue;
+                    const LPt p = {x - cx, y - cy, z - cz, r};
+                    LPt u[4] = {T[0], T[1], T[2], T[3]};
+                    u[kf] = p;
+                    const int64_t so = orient(u[0], u[1], u[2], u[3]);
+                    if (so != 0 && (so > 0) == (o > 0)) return false;
+                }
+        T[kf] = T[(kf + 1) & 3];
+        return true;
+    }
+    return false;
+}
+
 // The walk continues from the tetrahedron T it is given (a feasible basis:
 // q inside it), so a larger window resumes where a smaller one stopped.
 __device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz, int R,
@@ -204,30 +313,24 @@ __device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64
                 }
         const int64_t o = orient(T[0], T[1], T[2], T[3]);
         if (!found) {
-            // optimal: q's barycentric coordinates in T; a starting point
-            // may stay only with weight exactly 0 (q on the opposite face)
+            // optimal: q's barycentric coordinates in T
+            int64_t ol[4];
+            int nfar = 0, kf = -1;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 LPt u[4] = {T[0], T[1], T[2], T[3]};
                 u[k] = q0;
-                const int64_t ok = orient(u[0], u[1], u[2], u[3]);
-                if (T[k].rank >= P && ok != 0) return 0;
-                lam[k] = (double)ok / (double)o;
+                ol[k] = orient(u[0], u[1], u[2], u[3]);
+                lam[k] = (double)ol[k] / (double)o;
+                if (T[k].rank >= P) { ++nfar; kf = k; }
             }
             // the circumsphere must fit in the window: then no lattice
             // point outside the window is inside it
-            if (T[0].rank >= P || T[1].rank >= P || T[2].rank >= P || T[3].rank >= P) return 1;
-            const double rad = sqrt(r2) * (1.0 + 1e-12) + 1e-9;
-            const double lo[3] = {(double)(x0 - cx), (double)(y0 - cy), (double)(z0 - cz)};
-            const double hi[3] = {(double)(x1 - cx), (double)(y1 - cy), (double)(z1 - cz)};
-            const int64_t ext[3] = {S.x, S.y, S.z};
-            const int64_t cc[3] = {cx, cy, cz};
-            for (int m = 0; m < 3; ++m) {
-                // a window edge on the lattice boundary needs no margin
-                if (cc[m] + (int64_t)lo[m] > 0 && ctr[m] - rad <= lo[m] - 1.0) return 0;
-                if (cc[m] + (int64_t)hi[m] < ext[m] - 1 && ctr[m] + rad >= hi[m] + 1.0) return 0;
-            }
-            return 1;
+            if (nfar == 0) return sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1) ? 1 : 0;
+            // a starting point with weight above 0: q is outside the hull
+            // of the window's valid points; with weight 0: q is on a facet
+            if (nfar > 1 || ol[kf] != 0) return 0;
+            return across_facet(S, valid, cx, cy, cz, x0, x1, y0, y1, z0, z1, T, kf) ? 1 : 0;
         }
         // ratio test: leaving vertex k minimises lambda_k / d_k over d_k > 0,
         // with lambda_k = O_k(q) / O and d_k = O_k(e) / O (O_k: orientation
@@ -258,6 +361,266 @@ __device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64
     return 0;
 }
 
+// ---- Faces: the same program in a face's two free coordinates ----------
+
+struct LPt2 {
+    int64_t u, v;      // free coordinates relative to the query point
+    int64_t rank;
+};
+
+// Counter-clockwise orientation of (a, b, c): positive when counter-clockwise.
+// Coordinates differ by less than 2^12 (as for LPt), so 64 bits are exact.
+__device__ __forceinline__ int64_t orient2(const LPt2 &a, const LPt2 &b, const LPt2 &c) {
+    return (b.u - a.u) * (c.v - a.v) - (b.v - a.v) * (c.u - a.u);
+}
+
+__device__ int perturbed_sign2(const LPt2 (&t)[3], const LPt2 &e);
+
+// Sign of the 4 x 4 determinant with rows (u, v, w, 1) of t0, t1, t2, e under
+// the perturbed lifting w = u^2 + v^2 + d_rank: positive when e is inside the
+// circumcircle of the counter-clockwise triangle (t0, t1, t2). Translated so
+// that e is the origin, the unperturbed part is the 3 x 3 determinant of the
+// rows (p - e, |p - e|^2).
+__device__ int lifted_sign2(const LPt2 (&t)[3], const LPt2 &e) {
+    int64_t r[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        r[i][0] = t[i].u - e.u;
+        r[i][1] = t[i].v - e.v;
+        r[i][2] = r[i][0] * r[i][0] + r[i][1] * r[i][1];
+    }
+    const int64_t d0 = det3(r[0][0], r[0][1], r[0][2], r[1][0], r[1][1], r[1][2], r[2][0], r[2][1], r[2][2]);
+    if (d0 != 0) return d0 > 0 ? 1 : -1;
+    return perturbed_sign2(t, e);
+}
+
+// The sign when the unperturbed determinant is zero: the lifted entry of
+// point k of (t0, t1, t2, e) has the cofactor (-1)^k orient2(the other three,
+// in order); the lowest-ranked point with a non-zero cofactor decides.
+__device__ __noinline__ int perturbed_sign2(const LPt2 (&t)[3], const LPt2 &e) {
+    const LPt2 *p[4] = {&t[0], &t[1], &t[2], &e};
+    bool used[4] = {false, false, false, false};
+    for (int round = 0; round < 4; ++round) {
+        int k = -1;
+        for (int m = 0; m < 4; ++m)
+            if (!used[m] && (k < 0 || p[m]->rank < p[k]->rank)) k = m;
+        used[k] = true;
+        const LPt2 *q[3];
+        for (int m = 0, n = 0; m < 4; ++m)
+            if (m != k) q[n++] = p[m];
+        const int64_t o = orient2(*q[0], *q[1], *q[2]);
+        if (o != 0) {
+            const int64_t c = (k & 1) ? -o : o;
+            return c > 0 ? 1 : -1;
+        }
+    }
+    return 0;
+}
+
+// Circumcircle of T (centre and squared radius, FP64), for the filter.
+__device__ void circumcircle(const LPt2 (&T)[3], double (&ctr)[2], double &r2) {
+    const double bx = (double)(T[1].u - T[0].u), by = (double)(T[1].v - T[0].v);
+    const double cx = (double)(T[2].u - T[0].u), cy = (double)(T[2].v - T[0].v);
+    const double d = 2.0 * (bx * cy - by * cx);
+    const double b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    const double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
+    ctr[0] = ux + (double)T[0].u;
+    ctr[1] = uy + (double)T[0].v;
+    r2 = ux * ux + uy * uy;
+}
+
+// Sets T to three far starting points around q (counter-clockwise).
+__device__ void start_triangle(int64_t P, LPt2 (&T)[3]) {
+    const int64_t far[3][2] = {{kFar, 0}, {-kFar, kFar}, {-kFar, -kFar}};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T[k].u = far[k][0]; T[k].v = far[k][1];
+        T[k].rank = P + k;
+    }
+    if (orient2(T[0], T[1], T[2]) < 0) { const LPt2 s = T[0]; T[0] = T[1]; T[1] = s; }
+}
+
+// The face version of sphere_fits: the circle centred at ctr (free
+// coordinates relative to c) with squared radius r2 stays clear of the
+// lattice lines just outside the window [u0, u1] x [v0, v1] of the face.
+__device__ bool circle_fits(const double (&ctr)[2], double r2, int3 S, const int64_t (&c)[3], int a, int b,
+                            int64_t u0, int64_t u1, int64_t v0, int64_t v1) {
+    const int64_t ext[3] = {S.x, S.y, S.z};
+    const double rad = sqrt(r2) * (1.0 + 1e-12) + 1e-9;
+    const int ax[2] = {a, b};
+    const int64_t lo[2] = {u0 - c[a], v0 - c[b]}, hi[2] = {u1 - c[a], v1 - c[b]};
+    for (int m = 0; m < 2; ++m) {
+        const int64_t cm = c[ax[m]];
+        if (cm + lo[m] > 0 && ctr[m] - rad <= (double)lo[m] - 1.0) return false;
+        if (cm + hi[m] < ext[ax[m]] - 1 && ctr[m] + rad >= (double)hi[m] + 1.0) return false;
+    }
+    return true;
+}
+
+// across_facet on a face: q lies on the edge F opposite the starting point
+// T[kf] (weight exactly 0). Wrap across F to the valid window point D whose
+// circle through F holds no other point on that side; accept when that
+// triangle's circle holds no valid window point and fits in the window, or
+// when no valid point of the face lies strictly on the far side of F (F is
+// then on the hull of the face's points).
+__device__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b,
+                            int64_t u0, int64_t u1, int64_t v0, int64_t v1, LPt2 (&T)[3], int kf) {
+    const int64_t ext[3] = {S.x, S.y, S.z};
+    const LPt2 A = T[(kf + 1) % 3], B = T[(kf + 2) % 3];
+    const int64_t sf = orient2(A, B, T[kf]);
+    bool far_pt = false, have = false;
+    LPt2 D = A;
+    for (int64_t vv = v0; vv <= v1; ++vv)
+        for (int64_t uu = u0; uu <= u1; ++uu) {
+            int64_t pc[3] = {c[0], c[1], c[2]};
+            pc[a] = uu;
+            pc[b] = vv;
+            const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+            if (!valid[r] || r == A.rank || r == B.rank) continue;
+            const LPt2 p = {uu - c[a], vv - c[b], r};
+            const int64_t so = orient2(A, B, p);
+            if (so == 0) continue;
+            if ((so > 0) == (sf > 0)) { far_pt = true; continue; }
+            if (!have) { D = p; have = true; continue; }
+            LPt2 t3[3] = {A, B, D};
+            if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
+            if (lifted_sign2(t3, p) > 0) D = p;
+        }
+    if (have) {
+        LPt2 t3[3] = {A, B, D};
+        if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
+        bool empty = true;
+        for (int64_t vv = v0; vv <= v1 && empty; ++vv)
+            for (int64_t uu = u0; uu <= u1 && empty; ++uu) {
+                int64_t pc[3] = {c[0], c[1], c[2]};
+                pc[a] = uu;
+                pc[b] = vv;
+                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+                if (!valid[r] || r == A.rank || r == B.rank || r == D.rank) continue;
+                const LPt2 p = {uu - c[a], vv - c[b], r};
+                if (lifted_sign2(t3, p) > 0) empty = false;
+            }
+        double ctr[2], r2;
+        circumcircle(t3, ctr, r2);
+        if (empty && circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1)) {
+            T[kf] = D;
+            return true;
+        }
+    }
+    // no valid point of the face strictly on the far side of F (a
+    // whole-face scan, for faces of up to kHullScan2 points)
+    if (!far_pt && ext[a] * ext[b] <= kHullScan2) {
+        for (int64_t vv = 0; vv < ext[b]; ++vv)
+            for (int64_t uu = 0; uu < ext[a]; ++uu) {
+                int64_t pc[3] = {c[0], c[1], c[2]};
+                pc[a] = uu;
+                pc[b] = vv;
+                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+                if (!valid[r]) continue;
+                const LPt2 p = {uu - c[a], vv - c[b], r};
+                const int64_t so = orient2(A, B, p);
+                if (so != 0 && (so > 0) == (sf > 0)) return false;
+            }
+        T[kf] = A;
+        return true;
+    }
+    return false;
+}
+
+// The walk of `walk` on the face through c whose free axes are a < b: the
+// window is the square of radius R around c on that face. Points are
+// visited in rank order (axis b outer, axis a inner). Returns 1 with the
+// triangle and q's barycentric coordinates, or 0.
+__device__ int walk2(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b, int R,
+                     LPt2 (&T)[3], double (&lam)[3]) {
+    const int64_t P = (int64_t)S.x * S.y * S.z;
+    const int64_t ext[3] = {S.x, S.y, S.z};
+    const LPt2 q0 = {0, 0, -1};
+    const int64_t u0 = max(c[a] - R, (int64_t)0), u1 = min(c[a] + R, ext[a] - 1);
+    const int64_t v0 = max(c[b] - R, (int64_t)0), v1 = min(c[b] + R, ext[b] - 1);
+    for (int it = 0; it < kMaxPivots; ++it) {
+        double ctr[2], r2;
+        circumcircle(T, ctr, r2);
+        const double tol = 1e-9 * (r2 + 1.0);
+        LPt2 e;
+        bool found = false;
+        for (int64_t vv = v0; vv <= v1 && !found; ++vv)
+            for (int64_t uu = u0; uu <= u1 && !found; ++uu) {
+                int64_t pc[3] = {c[0], c[1], c[2]};
+                pc[a] = uu;
+                pc[b] = vv;
+                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+                if (!valid[r]) continue;
+                const double du = (double)(uu - c[a]) - ctr[0], dv = (double)(vv - c[b]) - ctr[1];
+                if (du * du + dv * dv > r2 + tol) continue;
+                if (T[0].rank == r || T[1].rank == r || T[2].rank == r) continue;
+                const LPt2 cand = {uu - c[a], vv - c[b], r};
+                if (lifted_sign2(T, cand) > 0) { e = cand; found = true; }
+            }
+        const int64_t o = orient2(T[0], T[1], T[2]);   // > 0: T is kept counter-clockwise
+        if (!found) {
+            int64_t ol[3];
+            int nfar = 0, kf = -1;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                LPt2 u[3] = {T[0], T[1], T[2]};
+                u[k] = q0;
+                ol[k] = orient2(u[0], u[1], u[2]);
+                lam[k] = (double)ol[k] / (double)o;
+                if (T[k].rank >= P) { ++nfar; kf = k; }
+            }
+            if (nfar == 0) return circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1) ? 1 : 0;
+            if (nfar > 1 || ol[kf] != 0) return 0;
+            return across_edge(S, valid, c, a, b, u0, u1, v0, v1, T, kf) ? 1 : 0;
+        }
+        int leave = -1;
+        int64_t bq = 0, be = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            LPt2 u[3] = {T[0], T[1], T[2]};
+            u[k] = e;
+            const int64_t oe = orient2(u[0], u[1], u[2]);
+            if (oe <= 0) continue;
+            u[k] = q0;
+            const int64_t oq = orient2(u[0], u[1], u[2]);
+            bool better = leave < 0;
+            if (!better) {
+                const int64_t lhs = oq * be, rhs = bq * oe;   // below 2^50
+                better = lhs < rhs || (lhs == rhs && T[k].rank < T[leave].rank);
+            }
+            if (better) { leave = k; bq = oq; be = oe; }
+        }
+        if (leave < 0) return 0;
+        T[leave] = e;
+        if (orient2(T[0], T[1], T[2]) < 0) { const LPt2 s = T[0]; T[0] = T[1]; T[1] = s; }
+    }
+    return 0;
+}
+
+// ---- Edges: nearest valid neighbours along the free axis a --------------
+__device__ int edge_interp(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a,
+                           int64_t (&vtx)[4], double (&lam)[4]) {
+    const int64_t ext[3] = {S.x, S.y, S.z};
+    int64_t pc[3] = {c[0], c[1], c[2]};
+    int64_t lo = -1, hi = -1;
+    for (int64_t t = c[a] - 1; t >= 0 && lo < 0; --t) {
+        pc[a] = t;
+        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) lo = t;
+    }
+    for (int64_t t = c[a] + 1; t < ext[a] && hi < 0; ++t) {
+        pc[a] = t;
+        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) hi = t;
+    }
+    if (lo < 0 || hi < 0) return 0;
+    pc[a] = lo;
+    vtx[0] = lattice_rank(S, pc[0], pc[1], pc[2]);
+    pc[a] = hi;
+    vtx[1] = lattice_rank(S, pc[0], pc[1], pc[2]);
+    lam[0] = (double)(hi - c[a]) / (double)(hi - lo);
+    lam[1] = (double)(c[a] - lo) / (double)(hi - lo);
+    return 1;
+}
+
 // One thread per lattice point: valid entries are copied (status 1),
 // missing ones take the barycentric interpolant over their Delaunay
 // tetrahedron (status 2) or stay missing (NaN, status 0).
@@ -272,15 +635,34 @@ __global__ void fill_delaunay_kernel(int3 S, const float *__restrict__ ends, con
             continue;
         }
         const int64_t cx = p % S.x, cy = (p / S.x) % S.y, cz = p / ((int64_t)S.x * S.y);
-        LPt T[4];
-        double lam[4];
-        int ok = 0;
-        // entries on the lattice's boundary faces have neighbours on one side
-        // only and stay missing
-        const bool interior = cx > 0 && cy > 0 && cz > 0 && cx < S.x - 1 && cy < S.y - 1 && cz < S.z - 1;
-        if (!interior) ok = -1;
-        start_tetrahedron(P, T);
-        for (int R = 2; R <= kMaxWindow && !ok; ++R) ok = walk(S, valid, cx, cy, cz, R, T, lam);
+        const int64_t c[3] = {cx, cy, cz};
+        const bool fixed[3] = {cx == 0 || cx == S.x - 1, cy == 0 || cy == S.y - 1, cz == 0 || cz == S.z - 1};
+        const int nfix = (int)fixed[0] + (int)fixed[1] + (int)fixed[2];
+        const bool flat = S.x == 1 || S.y == 1 || S.z == 1;
+        int64_t vtx[4] = {-1, -1, -1, -1};
+        double lam[4] = {0.0, 0.0, 0.0, 0.0};
+        int nv = 0, ok = 0;
+        if (flat || nfix == 3) {
+            ok = 0;                                   // no tetrahedra, or a corner
+        } else if (nfix == 0) {
+            LPt T[4];
+            start_tetrahedron(P, T);
+            for (int R = 2; R <= kMaxWindow && !ok; ++R) ok = walk(S, valid, cx, cy, cz, R, T, lam);
+            for (int k = 0; k < 4; ++k) vtx[k] = T[k].rank;
+            nv = 4;
+        } else if (nfix == 1) {
+            const int a = fixed[0] ? 1 : 0, b = fixed[2] ? 1 : 2;
+            LPt2 T2[3];
+            double l2[3];
+            start_triangle(P, T2);
+            for (int R = 2; R <= kMaxWindow2 && !ok; ++R) ok = walk2(S, valid, c, a, b, R, T2, l2);
+            for (int k = 0; k < 3; ++k) { vtx[k] = T2[k].rank; lam[k] = l2[k]; }
+            nv = 3;
+        } else {
+            const int a = !fixed[0] ? 0 : (!fixed[1] ? 1 : 2);
+            ok = edge_interp(S, valid, c, a, vtx, lam);
+            nv = 2;
+        }
         if (ok != 1) {
             const float nan = __int_as_float(0x7fc00000);
             out[3 * p] = nan; out[3 * p + 1] = nan; out[3 * p + 2] = nan;
@@ -288,11 +670,12 @@ __global__ void fill_delaunay_kernel(int3 S, const float *__restrict__ ends, con
             continue;
         }
         double acc[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t v = T[k].rank;
-            if (v >= P) continue;   // a starting point with weight 0
-            if (!BTO_IN_BOUNDS(v >= 0, nullptr)) continue;
+        for (int k = 0; k < nv; ++k) {
+            const int64_t v = vtx[k];
+            if (v < 0 || v >= P) {   // never: both walks reject starting points
+                (void)BTO_IN_BOUNDS(false, nullptr);
+                continue;
+            }
 #pragma unroll
             for (int d = 0; d < 3; ++d) acc[d] += lam[k] * (double)ends[3 * v + d];
         }

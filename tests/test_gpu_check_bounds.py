@@ -24,7 +24,7 @@ if ROOT not in sys.path:
 def scenarios():
     """Small intervals through every kernel family: ABC block (F3, F4, every
     particle leaves), a ragged turbulent block with exit locations, uneven
-    batched blocks untiled and tiled, lattice fill and stitching."""
+    batched blocks untiled and tiled, lattice and Delaunay fills, stitching."""
     import torch
     from paper_2004_02003_gb300 import bto, inputs
     torch.cuda.set_device(0)
@@ -93,6 +93,13 @@ def scenarios():
         out[tag + "path"] = path.cpu().numpy()
     out["fill_status"] = status.cpu().numpy()
     out["filled"] = filled.cpu().numpy()
+    # the Delaunay fill of the same lattice (interior, face and edge entries)
+    dfill = torch.empty_like(ends)
+    dstat = torch.empty_like(valid)
+    bto.bto_fill_delaunay(S, ends, valid, dfill, dstat)
+    torch.cuda.synchronize()
+    out["delaunay_status"] = dstat.cpu().numpy()
+    out["delaunay_filled"] = dfill.cpu().numpy()
     return out
 
 

@@ -47,7 +47,8 @@ def _gpu_fill(S, ends, valid):
 
 
 @pytest.mark.parametrize("S,frac,balls,seed", [((12, 11, 10), 0.08, 3, 11), ((9, 14, 8), 0.2, 0, 12),
-                                              ((10, 10, 10), 0.02, 5, 13), ((6, 5, 4), 0.3, 1, 14)])
+                                              ((10, 10, 10), 0.02, 5, 13), ((6, 5, 4), 0.3, 1, 14),
+                                              ((7, 9, 2), 0.25, 0, 15), ((20, 3, 16), 0.15, 2, 16)])
 def test_delaunay_fill_matches_oracle(S, frac, balls, seed):
     v = _holes(S, frac, seed, balls)
     X = oracle.lattice_coords(S, np.arange(int(np.prod(S))))
@@ -87,9 +88,6 @@ def test_delaunay_fill_affine_and_quadratic_closed_forms():
     n = 0
     for j in np.flatnonzero(~v):
         x = X[j].astype(int)
-        if np.any(x == 0) or np.any(x == np.array(S) - 1):
-            assert sq[j] == 0            # boundary faces stay missing
-            continue
         for a in range(3):
             lo, hi = x.copy(), x.copy()
             lo[a] -= 1; hi[a] += 1
@@ -102,3 +100,54 @@ def test_delaunay_fill_affine_and_quadratic_closed_forms():
                 n += 1
                 break
     assert n > 50
+
+
+def test_boundary_entries_and_flat_lattice():
+    """Entries on the lattice's faces and edges are filled over the face's
+    triangles and the edge's segments, as the oracle's tetrahedra give them;
+    corners stay missing; a lattice one point thick has no tetrahedra."""
+    S = (11, 10, 9)
+    rng = np.random.default_rng(17)
+    P = int(np.prod(S))
+    X = oracle.lattice_coords(S, np.arange(P)).astype(int)
+    face = np.any((X == 0) | (X == np.array(S) - 1), axis=1)
+    v = ~(face & (rng.random(P) < 0.35))           # holes on the faces only
+    ends = rng.standard_normal((P, 3)).astype(np.float32)
+    ends_in = np.where(v[:, None], ends, np.nan).astype(np.float32)
+    ref, st_o = oracle.fill_delaunay(S, ends_in.astype(np.float64), v)
+    got, st_g = _gpu_fill(S, ends_in, v)
+    assert np.array_equal(st_g, st_o)
+    fixed = ((X == 0) | (X == np.array(S) - 1)).sum(axis=1)
+    assert np.sum((st_o == 2) & (fixed == 1)) > 50 and np.sum((st_o == 2) & (fixed == 2)) > 5
+    assert np.all(st_o[(fixed == 3) & ~v] == 0)
+    filled = st_o == 2
+    assert np.max(np.abs(got[filled] - ref[filled])) <= 2e-6 * np.abs(ref[filled]).max()
+    # one point thick: nothing to interpolate over
+    S1 = (8, 6, 1)
+    v1 = rng.random(48) >= 0.25
+    g1, s1 = _gpu_fill(S1, np.zeros((48, 3), np.float32), v1)
+    assert np.all(s1[~v1] == 0) and np.all(np.isnan(g1[~v1])) and np.all(s1[v1] == 1)
+
+
+@pytest.mark.parametrize("S,k,seed", [((9, 8, 7), 12, 1), ((11, 10, 9), 15, 2)])
+def test_entries_on_the_hull_of_the_valid_points(S, k, seed):
+    """Valid points fill the half space x + y + z <= k, with half of the
+    plane x + y + z = k and 5% of the rest missing: missing entries on that
+    plane lie on facets of the hull, where the walk ends on a facet with a
+    far starting point at weight 0 and has to certify the facet (wrapping
+    across it to a Delaunay tetrahedron of the valid points); entries beyond
+    the plane are outside the hull and stay missing."""
+    P = int(np.prod(S))
+    X = oracle.lattice_coords(S, np.arange(P))
+    r = np.random.default_rng(seed)
+    t = X.sum(axis=1)
+    v = (t <= k) & ~((t == k) & (r.random(P) < 0.5)) & (r.random(P) > 0.05)
+    ends = r.standard_normal((P, 3)).astype(np.float32)
+    ends_in = np.where(v[:, None], ends, np.nan).astype(np.float32)
+    ref, st_o = oracle.fill_delaunay(S, ends_in.astype(np.float64), v)
+    got, st_g = _gpu_fill(S, ends_in, v)
+    assert np.array_equal(st_g, st_o)
+    on_plane = (t == k) & ~v
+    assert np.sum(on_plane & (st_o == 2)) > 10 and np.all(st_o[(t > k) & ~v] == 0)
+    filled = st_o == 2
+    assert np.max(np.abs(got[filled] - ref[filled])) <= 2e-6 * np.abs(ref[filled]).max()
