@@ -480,10 +480,7 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": "turb256: 256^3 cells as 2x2x2 blocks of 128^3, Fourier turbulence (64 modes), "
-                        f"stride {args.stride} ({P:,} particles), interval 100, dt=0.25 cell/max|u|",
-            "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
-            "field_layout": args.layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
+            **workload_config(args.stride, P, nb, L, dt, args.layout, field_bytes_cycle),
             "ingest": bool(args.ingest),
             "l2": f"inputs larger than L2: each cycle reads a 206 MB field; {nf} distinct fields resident",
             "launch": ctx.launch(),
@@ -1313,6 +1310,16 @@ def oracle_other_configs():
     return res
 
 
+def workload_config(stride, P, nb, L, dt, layout, field_bytes_cycle):
+    """The keys that define the benchmark's workload, shared by both arms."""
+    return {
+        "workload": "turb256: 256^3 cells as 2x2x2 blocks of 128^3, Fourier turbulence (64 modes), "
+                    f"stride {stride} ({P:,} particles), interval {L}, dt=0.25 cell/max|u|",
+        "blocks": nb, "particles": P, "interval_cycles": L, "dt": dt,
+        "field_layout": layout.upper() + "_AOS", "field_bytes_per_cycle": field_bytes_cycle,
+    }
+
+
 def run_reference(args):
     """The oracle timed as the reference arm (rank 0 only, bounded sample)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -1326,6 +1333,7 @@ def run_reference(args):
     h = 1.0 / GLOBAL_CELLS
     dt = 0.25 * h
     g = oracle.Grid.make((BLOCK_CELLS,) * 3, (0, 0, 0), (h, h, h))
+    nb = len(block_layout(0, 1)[0])
     # a bounded sample per step: 8192 particles of block 0 over the full interval
     rng = np.random.default_rng(SEED)
     ids = np.sort(rng.choice(oracle.num_seeds(g, STRIDE), size=8192, replace=False))
@@ -1352,7 +1360,8 @@ def run_reference(args):
         "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "turb256 (bounded sample: 8192 random particles of block 0, full 100-cycle interval)"},
+        "config": workload_config(STRIDE, nb * oracle.num_seeds(g, STRIDE), nb, INTERVAL, dt, "f3",
+                                  nb * (BLOCK_CELLS + 1) ** 3 * 12),
         "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": "8192 random particles of block 0 of 8, all 100 cycles, per step"},
         "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
