@@ -556,6 +556,11 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     L = INTERVAL
     nb = len(ext)
     res = {}
+    # (0) end to end on the headline's own context, right after the headline:
+    # fields copied from pinned host memory every cycle, basis flows copied
+    # back every interval; copies overlap compute on a second stream with a
+    # two-slot device ring.
+    res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb, world)
     # (1) plain: one single-block context per block, one launch per block and cycle
     plain = [bto.Context(ext[b], org[b], spc[b], STRIDE, L) for b in range(nb)]
     shape = ctx.launch()
@@ -651,11 +656,6 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
     res["batched"] = batched_leg(args, dev, stream, rank, world)
     if rank == 0 and not args.no_large:
         res["large"] = large_leg(args, dev, stream)
-
-    # (5) end to end: fields copied from pinned host memory every cycle,
-    # basis flows copied back every interval; copies overlap compute on a
-    # second stream with a two-slot device ring.
-    res["e2e"] = e2e(args, ctx, fields, dt, dev, stream, nb, world)
     return res
 
 
