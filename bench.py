@@ -539,6 +539,9 @@ def summary(res):
     return {"value": get("value"), "frac": get("roofline", "frac"), "graph": get("graph_value"),
             "batched_value": get("batched", "batched_value"), "batched_frac": get("batched", "roofline", "frac"),
             "large_value": get("large", "batched_value"), "large_frac": get("large", "roofline", "frac"),
+            "accuracy_percent_lattice_delaunay": [
+                get("accuracy_vs_global", "reconstructed", "lattice", "accuracy_percent_C_h"),
+                get("accuracy_vs_global", "reconstructed", "delaunay", "accuracy_percent_C_h")],
             "large_accuracy_percent_lattice_delaunay": [iv[0].get("accuracy_percent"),
                                                         (iv[0].get("delaunay") or {}).get("accuracy_percent")],
             "adjoint_fwd_bwd_vs_plain": get("adjoint", "forward_backward_vs_plain"),
@@ -647,6 +650,7 @@ def extras(args, ctx, fields, gfields, table, out, exit_ref, psteps, dt, dev, st
             "bto_valid_but_global_invalid": int((ok & (gv[gid] == 0)).sum()),
             "max_valid_end_deviation_cells": dev_cells,
             "global_particle_steps": count_particle_steps(gce, L),
+            "reconstructed": reconstruction_metrics(bto, GS, h, STRIDE, gid, be, bv, ge, gv, dev),
         }
 
     # (4) adjoint and batched workloads against the plain path (rank 0)
@@ -1125,6 +1129,42 @@ def large_leg(args, dev, stream):
             "intervals": report,
             "greatest_max_l2": max(maxes), "average_max_l2": float(np.mean(maxes)),
             "pathlines_vs_rk4_ground_truth": path_err}
+
+
+def reconstruction_metrics(bto, GS, h, stride, gid, be, bv, ge, gv, dev):
+    """The paper's accuracy metrics (Sec. 4.3) of one interval's BTO basis
+    flows against the global map after the missing entries of the global seed
+    lattice (GS^3) are filled, by the lattice fill and by the Delaunay fill:
+    total average L2 and max L2 over the entries valid in the global map and
+    filled, Accuracy% with C = h and with C = stride * h (the seed spacing)."""
+    import torch
+    P = GS ** 3
+    lat_e = torch.full((P, 3), float("nan"), dtype=torch.float32, device=dev)
+    lat_v = torch.zeros((P,), dtype=torch.uint8, device=dev)
+    gidt = torch.from_numpy(gid).to(dev)
+    lat_e[gidt] = torch.from_numpy(be.astype(np.float32)).to(dev)
+    lat_v[gidt] = torch.from_numpy(bv).to(dev)
+    gvt = torch.from_numpy(gv).to(dev) == 1
+    get = torch.from_numpy(ge).to(dev)
+    outm = {}
+    for name, fill in (("lattice", bto.bto_fill_lattice), ("delaunay", bto.bto_fill_delaunay)):
+        f = torch.empty_like(lat_e)
+        st = torch.empty_like(lat_v)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fill((GS, GS, GS), lat_e, lat_v, f, st)
+        e1.record()
+        torch.cuda.synchronize()
+        okm = gvt & (st > 0)
+        err = (f[okm].double() - get[okm]).norm(dim=1)
+        l2, mx = err.mean().item(), err.max().item()
+        outm[name] = {"total_average_l2": l2, "max_l2": mx,
+                      "accuracy_percent_C_h": (h - l2) / h * 100.0,
+                      "accuracy_percent_C_seed_spacing": (stride * h - l2) / (stride * h) * 100.0,
+                      "filled": int((st == 2).sum().item()), "still_missing": int((st == 0).sum().item()),
+                      "still_missing_valid_in_global_map": int(((st == 0) & gvt).sum().item()),
+                      "fill_ms": e0.elapsed_time(e1)}
+    return outm
 
 
 def delaunay_fill_report(bto, G, h, lat_e, lat_v, gout, filled, status, ok, stream):

@@ -137,10 +137,31 @@ constexpr int64_t kFar = 1024;   // distance of the four starting points, lattic
 constexpr int kMaxPivots = 512;
 constexpr int kMaxWindow = 6;      // largest window radius, lattice units
 constexpr int kMaxWindow2 = 12;    // on a face (a window of 25 x 25 points)
-// Largest lattice (face) scanned whole to show that a facet (edge) through
-// the query point bounds the hull of all valid points.
-constexpr int64_t kHullScan3 = (int64_t)1 << 21;
-constexpr int64_t kHullScan2 = (int64_t)1 << 20;
+// Work limit (rows plus points) of the scan that shows that a facet (edge)
+// through the query point bounds the hull of all valid points.
+constexpr int64_t kHullScanWork = (int64_t)1 << 22;
+
+// floor(n / d) and ceil(n / d) for d > 0.
+__device__ __forceinline__ int64_t floor_div(int64_t n, int64_t d) { return n >= 0 ? n / d : -((-n + d - 1) / d); }
+__device__ __forceinline__ int64_t ceil_div(int64_t n, int64_t d) { return n >= 0 ? (n + d - 1) / d : -((-n) / d); }
+
+// The integers t in [lo, hi] with a t + b > 0, as [t0, t1]; false when none.
+__device__ __forceinline__ bool positive_range(int64_t a, int64_t b, int64_t lo, int64_t hi, int64_t &t0,
+                                               int64_t &t1) {
+    if (a == 0) {
+        t0 = lo;
+        t1 = hi;
+        return b > 0 && lo <= hi;
+    }
+    if (a > 0) {
+        t0 = max(lo, floor_div(-b, a) + 1);
+        t1 = hi;
+    } else {
+        t0 = lo;
+        t1 = min(hi, ceil_div(b, -a) - 1);
+    }
+    return t0 <= t1;
+}
 
 // Outcome of one walk in a window of radius R around the lattice point c:
 // 1 and the tetrahedron with q's barycentric coordinates, or 0 (no result
@@ -212,7 +233,7 @@ __device__ bool sphere_fits(const double (&ctr)[3], double r2, int3 S, int64_t c
 // the other side whose sphere through F holds no other such point gives a
 // tetrahedron whose sphere holds no valid window point at all and fits in
 // the window, or (b) no valid point of the lattice lies strictly on the far
-// side of F (F is then on the hull). Either way T[kf] is replaced by a
+// side of F (F is then on the hull; shown within a work limit). Either way T[kf] is replaced by a
 // valid point (D, or a vertex of F) with weight 0.
 __device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz,
                              int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0, int64_t z1, LPt (&T)[4],
@@ -257,20 +278,34 @@ __device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t 
             return true;
         }
     }
-    // (b): no valid point of the lattice strictly on the far side of F (a
-    // whole-lattice scan, for lattices of up to kHullScan3 points)
-    if (!far_pt && (int64_t)S.x * S.y * S.z <= kHullScan3) {
+    // (b): no valid point of the lattice strictly on the far side of F. The
+    // orientation with p in place of the starting point is affine in p,
+    // n.p + d, so each lattice row holds its far-side points in one interval
+    // and only those are visited (within kHullScanWork rows and points).
+    if (!far_pt) {
+        LPt u[4] = {T[0], T[1], T[2], T[3]};
+        const LPt o0 = {0, 0, 0, -1}, ex = {1, 0, 0, -1}, ey = {0, 1, 0, -1}, ez = {0, 0, 1, -1};
+        u[kf] = o0;
+        const int64_t d = orient(u[0], u[1], u[2], u[3]);
+        u[kf] = ex;
+        const int64_t nx = orient(u[0], u[1], u[2], u[3]) - d;
+        u[kf] = ey;
+        const int64_t ny = orient(u[0], u[1], u[2], u[3]) - d;
+        u[kf] = ez;
+        const int64_t nz = orient(u[0], u[1], u[2], u[3]) - d;
+        const int64_t sg = o > 0 ? 1 : -1;
+        int64_t work = 0;
         for (int64_t z = 0; z < S.z; ++z)
-            for (int64_t y = 0; y < S.y; ++y)
-                for (int64_t x = 0; x < S.x; ++x) {
-                    const int64_t r = lattice_rank(S, x, y, z);
-                    if (!valid[r]) continue;
-                    const LPt p = {x - cx, y - cy, z - cz, r};
-                    LPt u[4] = {T[0], T[1], T[2], T[3]};
-                    u[kf] = p;
-                    const int64_t so = orient(u[0], u[1], u[2], u[3]);
-                    if (so != 0 && (so > 0) == (o > 0)) return false;
+            for (int64_t y = 0; y < S.y; ++y) {
+                if (++work > kHullScanWork) return false;
+                int64_t t0, t1;
+                if (!positive_range(sg * nx, sg * (ny * (y - cy) + nz * (z - cz) + d), -cx, (int64_t)S.x - 1 - cx, t0, t1))
+                    continue;
+                for (int64_t t = t0; t <= t1; ++t) {
+                    if (++work > kHullScanWork) return false;
+                    if (valid[lattice_rank(S, t + cx, y, z)]) return false;
                 }
+            }
         T[kf] = T[(kf + 1) & 3];
         return true;
     }
@@ -507,20 +542,27 @@ __device__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int
             return true;
         }
     }
-    // no valid point of the face strictly on the far side of F (a
-    // whole-face scan, for faces of up to kHullScan2 points)
-    if (!far_pt && ext[a] * ext[b] <= kHullScan2) {
-        for (int64_t vv = 0; vv < ext[b]; ++vv)
-            for (int64_t uu = 0; uu < ext[a]; ++uu) {
+    // no valid point of the face strictly on the far side of F, visiting
+    // only the far-side interval of each row (orient2(A, B, p) is affine in
+    // p), within kHullScanWork rows and points
+    if (!far_pt) {
+        const LPt2 o0 = {0, 0, -1}, eu = {1, 0, -1}, ev = {0, 1, -1};
+        const int64_t d = orient2(A, B, o0);
+        const int64_t nu = orient2(A, B, eu) - d, nv = orient2(A, B, ev) - d;
+        const int64_t sg = sf > 0 ? 1 : -1;
+        int64_t work = 0;
+        for (int64_t vv = 0; vv < ext[b]; ++vv) {
+            if (++work > kHullScanWork) return false;
+            int64_t t0, t1;
+            if (!positive_range(sg * nu, sg * (nv * (vv - c[b]) + d), -c[a], ext[a] - 1 - c[a], t0, t1)) continue;
+            for (int64_t t = t0; t <= t1; ++t) {
+                if (++work > kHullScanWork) return false;
                 int64_t pc[3] = {c[0], c[1], c[2]};
-                pc[a] = uu;
+                pc[a] = t + c[a];
                 pc[b] = vv;
-                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
-                if (!valid[r]) continue;
-                const LPt2 p = {uu - c[a], vv - c[b], r};
-                const int64_t so = orient2(A, B, p);
-                if (so != 0 && (so > 0) == (sf > 0)) return false;
+                if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) return false;
             }
+        }
         T[kf] = A;
         return true;
     }
