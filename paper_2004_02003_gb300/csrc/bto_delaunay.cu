@@ -10,16 +10,17 @@
 //     minimise   sum_i lambda_i w(j_i)
 //     subject to sum_i lambda_i j_i = q,  sum_i lambda_i = 1,  lambda >= 0,
 // whose optimal lambda are q's barycentric coordinates in that tetrahedron.
-// Each thread solves this program for one missing lattice point by the
-// simplex method over the valid points of a window around it: the basis is
-// a tetrahedron holding q; a point inside the tetrahedron's circumsphere
-// (below the plane through its lifted vertices) has a negative reduced
-// cost and enters; the ratio test picks the vertex that leaves so that q
-// stays inside. It starts from four far points around q and stops when no
-// window point lies inside the circumsphere. The result is the Delaunay
-// tetrahedron of all valid points when its circumsphere fits in the window
-// (no lattice point outside the window can then lie inside it); otherwise
-// the window grows (radius 2 to 6 lattice units) and the walk restarts.
+// Each warp solves this program for one missing lattice point at a time by
+// the simplex method over the valid points of a window around it (the
+// lanes share out the window's points): the basis is a tetrahedron holding
+// q; a point inside the tetrahedron's circumsphere (below the plane through
+// its lifted vertices) has a negative reduced cost and enters; the ratio
+// test picks the vertex that leaves so that q stays inside. It starts from
+// four far points around q and stops when no window point lies inside the
+// circumsphere. The result is the Delaunay tetrahedron of all valid points
+// when its circumsphere fits in the window (no lattice point outside the
+// window can then lie inside it); otherwise the window grows (radius 2 to
+// 6 lattice units) and the walk resumes.
 //
 // Entries on the lattice's outer faces lie on the hull of the valid points.
 // There the face's plane supports the lifted point set, so the tetrahedra
@@ -73,12 +74,12 @@ __device__ __forceinline__ int64_t orient(const LPt &a, const LPt &b, const LPt 
                 d.z - a.z);
 }
 
-__device__ int perturbed_sign(const LPt (&t)[4], const LPt &e);
+__device__ __noinline__ int perturbed_sign(const LPt (&t)[4], const LPt &e);
 
 // Sign of the 5 x 5 determinant with rows (x, y, z, w, 1) of t0..t3, e
 // under the perturbed lifting: negative when e is inside the circumsphere of
 // the positively oriented tetrahedron (t0, t1, t2, t3).
-__device__ int lifted_sign(const LPt (&t)[4], const LPt &e) {
+__device__ __noinline__ int lifted_sign(const LPt (&t)[4], const LPt &e) {
     // unperturbed: rows (p - e, |p - e|^2) of the tetrahedron, expanded
     // along the squared-length column
     int64_t r[4][4];
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool positive_range(int64_t a, int64_t b, int64_t lo,
 // larger than the window, or the pivot limit).
 // Circumsphere of T (centre and squared radius, FP64), for the filter that
 // spares most points the exact predicate.
-__device__ void circumsphere(const LPt (&T)[4], double (&ctr)[3], double &r2) {
+__device__ __noinline__ void circumsphere(const LPt (&T)[4], double (&ctr)[3], double &r2) {
     double A[3][3], b[3];
     const LPt &a = T[0];
     for (int m = 0; m < 3; ++m) {
@@ -225,6 +226,91 @@ __device__ bool sphere_fits(const double (&ctr)[3], double r2, int3 S, int64_t c
     return true;
 }
 
+// Every routine from here on is warp-cooperative: the 32 lanes of a warp
+// solve one missing entry together. They hold the same simplex, split the
+// window's points between them (point k of the window goes to lane k mod
+// 32, k in rank order), and combine their findings with warp reductions,
+// so every decision is warp-uniform and equal to that of a serial scan in
+// rank order.
+constexpr unsigned kAll = 0xffffffffu;
+constexpr int64_t kNone = INT64_MAX;
+
+__device__ __forceinline__ int64_t warp_min(int64_t v) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, (int64_t)__shfl_xor_sync(kAll, (long long)v, o));
+    return v;
+}
+__device__ __forceinline__ int64_t warp_max(int64_t v) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(kAll, (long long)v, o));
+    return v;
+}
+__device__ __forceinline__ LPt shfl_xor_pt(const LPt &p, int o) {
+    LPt r;
+    r.x = __shfl_xor_sync(kAll, (long long)p.x, o);
+    r.y = __shfl_xor_sync(kAll, (long long)p.y, o);
+    r.z = __shfl_xor_sync(kAll, (long long)p.z, o);
+    r.rank = __shfl_xor_sync(kAll, (long long)p.rank, o);
+    return r;
+}
+
+__device__ __forceinline__ void positive_orientation(LPt (&t)[4]) {
+    if (orient(t[0], t[1], t[2], t[3]) < 0) { const LPt s = t[0]; t[0] = t[1]; t[1] = s; }
+}
+
+// A lane's walk over a window of wx x wy x wz points in rank order: points
+// k = lane, lane + 32, ..., with offsets (x, y, z) inside the window kept
+// by additions (a window holds at most 25 x 25 or 13 x 13 x 13 points, and
+// a lattice at most 2^31, so 32-bit indices suffice).
+struct WinIter {
+    int wx, wy, k, x, y, z;
+    __device__ WinIter(int wx_, int wy_, int start) : wx(wx_), wy(wy_), k(start) {
+        x = start % wx;
+        const int q = start / wx;
+        y = q % wy;
+        z = q / wy;
+    }
+    __device__ __forceinline__ void step() {
+        k += 32;
+        x += 32;
+        while (x >= wx) {
+            x -= wx;
+            if (++y == wy) { y = 0; ++z; }
+        }
+    }
+};
+
+// Pivot rule. The first kDeepPivots pivots enter the point deepest inside
+// the circumsphere (largest r^2 - |p - c|^2 in FP32, ties to the lowest
+// rank), which reaches q's simplex in few pivots; later pivots take the
+// lowest-ranked point inside (Bland's rule), which cannot cycle, so every
+// walk ends. Either way the entering point passes the exact predicate and
+// the walk stops only when no window point is inside the circumsphere.
+constexpr int kDeepPivots = 64;
+
+// Warp-maximum key of a candidate: the FP32 depth's bits made monotone in
+// the high word, the complement of the rank in the low word (ranks are
+// below 2^31); 0 means none.
+__device__ __forceinline__ unsigned long long depth_key(float depth, int64_t rank) {
+    const unsigned bits = __float_as_uint(depth);
+    const unsigned mono = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+    return ((unsigned long long)mono << 32) | (0xffffffffu - (unsigned)rank);
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(kAll, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// Lattice coordinates of the point of rank r (r < 2^31).
+__device__ __forceinline__ void rank_coords(int3 S, int64_t r, int64_t (&p)[3]) {
+    const int rr = (int)r;
+    p[0] = rr % S.x;
+    const int q = rr / S.x;
+    p[1] = q % S.y;
+    p[2] = q / S.y;
+}
+
 // The walk ended with one starting point (vertex kf of T) at weight exactly
 // 0: q lies on the facet F of the other three vertices, and no window point
 // is inside the sphere through F and the far starting point. F is a facet
@@ -233,47 +319,62 @@ __device__ bool sphere_fits(const double (&ctr)[3], double r2, int3 S, int64_t c
 // the other side whose sphere through F holds no other such point gives a
 // tetrahedron whose sphere holds no valid window point at all and fits in
 // the window, or (b) no valid point of the lattice lies strictly on the far
-// side of F (F is then on the hull; shown within a work limit). Either way T[kf] is replaced by a
-// valid point (D, or a vertex of F) with weight 0.
-__device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz,
+// side of F (F is then on the hull; shown within a work limit). Either way
+// T[kf] is replaced by a valid point (D, or a vertex of F) with weight 0.
+// Spheres through F order the points beyond it (a point inside the sphere
+// through F and D comes before D), so the lanes' candidates D combine into
+// the first one in any order.
+__device__ __noinline__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz,
                              int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0, int64_t z1, LPt (&T)[4],
                              int kf) {
+    const int lane = threadIdx.x & 31;
     const int64_t o = orient(T[0], T[1], T[2], T[3]);
+    const int wx = (int)(x1 - x0 + 1), wy = (int)(y1 - y0 + 1), W = wx * wy * (int)(z1 - z0 + 1);
     bool far_pt = false, have = false;
     LPt D = T[(kf + 1) & 3];
-    for (int64_t z = z0; z <= z1; ++z)
-        for (int64_t y = y0; y <= y1; ++y)
-            for (int64_t x = x0; x <= x1; ++x) {
-                const int64_t r = lattice_rank(S, x, y, z);
-                if (!valid[r] || T[0].rank == r || T[1].rank == r || T[2].rank == r || T[3].rank == r) continue;
-                const LPt p = {x - cx, y - cy, z - cz, r};
-                LPt u[4] = {T[0], T[1], T[2], T[3]};
-                u[kf] = p;
-                const int64_t so = orient(u[0], u[1], u[2], u[3]);
-                if (so == 0) continue;
-                if ((so > 0) == (o > 0)) { far_pt = true; continue; }
-                if (!have) { D = p; have = true; continue; }
-                LPt t4[4] = {T[0], T[1], T[2], T[3]};
-                t4[kf] = D;
-                if (orient(t4[0], t4[1], t4[2], t4[3]) < 0) { const LPt sw = t4[0]; t4[0] = t4[1]; t4[1] = sw; }
-                if (lifted_sign(t4, p) < 0) D = p;
-            }
+    for (WinIter w(wx, wy, lane); w.k < W; w.step()) {
+        const int64_t x = x0 + w.x, y = y0 + w.y, z = z0 + w.z;
+        const int64_t r = lattice_rank(S, x, y, z);
+        if (!valid[r] || T[0].rank == r || T[1].rank == r || T[2].rank == r || T[3].rank == r) continue;
+        const LPt p = {x - cx, y - cy, z - cz, r};
+        LPt u[4] = {T[0], T[1], T[2], T[3]};
+        u[kf] = p;
+        const int64_t so = orient(u[0], u[1], u[2], u[3]);
+        if (so == 0) continue;
+        if ((so > 0) == (o > 0)) { far_pt = true; continue; }
+        if (!have) { D = p; have = true; continue; }
+        LPt t4[4] = {T[0], T[1], T[2], T[3]};
+        t4[kf] = D;
+        positive_orientation(t4);
+        if (lifted_sign(t4, p) < 0) D = p;
+    }
+    far_pt = __any_sync(kAll, far_pt);
+    for (int off = 16; off > 0; off >>= 1) {
+        const LPt Do = shfl_xor_pt(D, off);
+        const bool ho = __shfl_xor_sync(kAll, (int)have, off) != 0;
+        if (!ho || Do.rank == D.rank) continue;
+        if (!have) { D = Do; have = true; continue; }
+        LPt t4[4] = {T[0], T[1], T[2], T[3]};
+        t4[kf] = D;
+        positive_orientation(t4);
+        if (lifted_sign(t4, Do) < 0) D = Do;
+    }
     if (have) {
         LPt t4[4] = {T[0], T[1], T[2], T[3]};
         t4[kf] = D;
-        if (orient(t4[0], t4[1], t4[2], t4[3]) < 0) { const LPt sw = t4[0]; t4[0] = t4[1]; t4[1] = sw; }
-        bool empty = true;
-        for (int64_t z = z0; z <= z1 && empty; ++z)
-            for (int64_t y = y0; y <= y1 && empty; ++y)
-                for (int64_t x = x0; x <= x1 && empty; ++x) {
-                    const int64_t r = lattice_rank(S, x, y, z);
-                    if (!valid[r] || t4[0].rank == r || t4[1].rank == r || t4[2].rank == r || t4[3].rank == r) continue;
-                    const LPt p = {x - cx, y - cy, z - cz, r};
-                    if (lifted_sign(t4, p) < 0) empty = false;
-                }
+        positive_orientation(t4);
+        bool inside = false;
+        for (WinIter w(wx, wy, lane); w.k < W && !inside; w.step()) {
+            const int64_t x = x0 + w.x, y = y0 + w.y, z = z0 + w.z;
+            const int64_t r = lattice_rank(S, x, y, z);
+            if (!valid[r] || t4[0].rank == r || t4[1].rank == r || t4[2].rank == r || t4[3].rank == r) continue;
+            const LPt p = {x - cx, y - cy, z - cz, r};
+            inside = lifted_sign(t4, p) < 0;
+        }
+        inside = __any_sync(kAll, inside);
         double ctr[3], r2;
         circumsphere(t4, ctr, r2);
-        if (empty && sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1)) {
+        if (!inside && sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1)) {
             T[kf] = D;
             return true;
         }
@@ -294,18 +395,20 @@ __device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t 
         u[kf] = ez;
         const int64_t nz = orient(u[0], u[1], u[2], u[3]) - d;
         const int64_t sg = o > 0 ? 1 : -1;
+        const int64_t rows = (int64_t)S.y * S.z, budget = kHullScanWork / 32;
         int64_t work = 0;
-        for (int64_t z = 0; z < S.z; ++z)
-            for (int64_t y = 0; y < S.y; ++y) {
-                if (++work > kHullScanWork) return false;
-                int64_t t0, t1;
-                if (!positive_range(sg * nx, sg * (ny * (y - cy) + nz * (z - cz) + d), -cx, (int64_t)S.x - 1 - cx, t0, t1))
-                    continue;
-                for (int64_t t = t0; t <= t1; ++t) {
-                    if (++work > kHullScanWork) return false;
-                    if (valid[lattice_rank(S, t + cx, y, z)]) return false;
-                }
+        bool stop = false;                          // a far-side valid point, or out of budget
+        for (int64_t row = lane; row < rows && !stop; row += 32) {
+            const int64_t y = (int)row % S.y, z = (int)row / S.y;
+            if (++work > budget) { stop = true; break; }
+            int64_t t0, t1;
+            if (!positive_range(sg * nx, sg * (ny * (y - cy) + nz * (z - cz) + d), -cx, (int64_t)S.x - 1 - cx, t0, t1))
+                continue;
+            for (int64_t t = t0; t <= t1; ++t) {
+                if (++work > budget || valid[lattice_rank(S, t + cx, y, z)]) { stop = true; break; }
             }
+        }
+        if (__any_sync(kAll, stop)) return false;
         T[kf] = T[(kf + 1) & 3];
         return true;
     }
@@ -314,40 +417,57 @@ __device__ bool across_facet(int3 S, const uint8_t *__restrict__ valid, int64_t 
 
 // The walk continues from the tetrahedron T it is given (a feasible basis:
 // q inside it), so a larger window resumes where a smaller one stopped.
-__device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz, int R,
+__device__ __noinline__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64_t cy, int64_t cz, int R,
                     LPt (&T)[4], double (&lam)[4]) {
+    const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t)S.x * S.y * S.z;
     const LPt q0 = {0, 0, 0, -1};
     const int64_t x0 = max(cx - R, (int64_t)0), x1 = min(cx + R, (int64_t)S.x - 1);
     const int64_t y0 = max(cy - R, (int64_t)0), y1 = min(cy + R, (int64_t)S.y - 1);
     const int64_t z0 = max(cz - R, (int64_t)0), z1 = min(cz + R, (int64_t)S.z - 1);
+    const int wx = (int)(x1 - x0 + 1), wy = (int)(y1 - y0 + 1), W = wx * wy * (int)(z1 - z0 + 1);
     for (int it = 0; it < kMaxPivots; ++it) {
         // entering point: the lowest-ranked valid window point inside the
-        // circumsphere of T (points are visited in rank order). A point
-        // clearly outside by the FP64 distance to the centre (margin far
-        // above its rounding error) is skipped; every other point gets the
-        // exact predicate, so the choice is the exact one.
+        // circumsphere of T (each lane takes the first of its points in rank
+        // order, the warp the least of those). A point clearly outside by
+        // its FP32 distance to the centre is skipped. T holds q, so the
+        // centre lies within r of q, and near the sphere the squared
+        // distance's rounding error stays below 1e-6 r^2: with the margin
+        // 1e-4 r^2 + 1e-2 only points strictly outside are skipped; every
+        // other point gets the exact predicate, so the choice is the exact
+        // one.
         double ctr[3], r2;
         circumsphere(T, ctr, r2);
-        const double tol = 1e-9 * (r2 + 1.0);
-        LPt e;
-        bool found = false;
-        for (int64_t z = z0; z <= z1 && !found; ++z)
-            for (int64_t y = y0; y <= y1 && !found; ++y)
-                for (int64_t x = x0; x <= x1 && !found; ++x) {
-                    if (!valid[lattice_rank(S, x, y, z)]) continue;
-                    const double dx = (double)(x - cx) - ctr[0], dy = (double)(y - cy) - ctr[1],
-                                 dz = (double)(z - cz) - ctr[2];
-                    if (dx * dx + dy * dy + dz * dz > r2 + tol) continue;
-                    const LPt c = {x - cx, y - cy, z - cz, lattice_rank(S, x, y, z)};
-                    bool inT = false;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) inT |= T[k].rank == c.rank;
-                    if (inT) continue;
-                    if (lifted_sign(T, c) < 0) { e = c; found = true; }
-                }
+        const float fc0 = (float)ctr[0], fc1 = (float)ctr[1], fc2 = (float)ctr[2];
+        const float fr2 = (float)r2 * (1.0f + 1e-4f) + 1e-2f;
+        const bool deep = it < kDeepPivots;
+        int64_t best = kNone;
+        unsigned long long bkey = 0;
+        for (WinIter w(wx, wy, lane); w.k < W; w.step()) {
+            const int64_t x = x0 + w.x, y = y0 + w.y, z = z0 + w.z;
+            const int64_t r = lattice_rank(S, x, y, z);
+            if (!valid[r]) continue;
+            const float dx = (float)(x - cx) - fc0, dy = (float)(y - cy) - fc1, dz = (float)(z - cz) - fc2;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 > fr2) continue;
+            if (T[0].rank == r || T[1].rank == r || T[2].rank == r || T[3].rank == r) continue;
+            const LPt p = {x - cx, y - cy, z - cz, r};
+            if (deep) {
+                const unsigned long long key = depth_key((float)r2 - d2, r);
+                if (key > bkey && lifted_sign(T, p) < 0) bkey = key;
+            } else if (lifted_sign(T, p) < 0) {
+                best = r;
+                break;
+            }
+        }
+        if (deep) {
+            bkey = warp_max_u64(bkey);
+            best = bkey ? (int64_t)(0xffffffffu - (unsigned)(bkey & 0xffffffffu)) : kNone;
+        } else {
+            best = warp_min(best);
+        }
         const int64_t o = orient(T[0], T[1], T[2], T[3]);
-        if (!found) {
+        if (best == kNone) {
             // optimal: q's barycentric coordinates in T
             int64_t ol[4];
             int nfar = 0, kf = -1;
@@ -367,6 +487,9 @@ __device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64
             if (nfar > 1 || ol[kf] != 0) return 0;
             return across_facet(S, valid, cx, cy, cz, x0, x1, y0, y1, z0, z1, T, kf) ? 1 : 0;
         }
+        int64_t bc[3];
+        rank_coords(S, best, bc);
+        const LPt e = {bc[0] - cx, bc[1] - cy, bc[2] - cz, best};
         // ratio test: leaving vertex k minimises lambda_k / d_k over d_k > 0,
         // with lambda_k = O_k(q) / O and d_k = O_k(e) / O (O_k: orientation
         // with vertex k replaced); ties go to the lowest rank
@@ -391,7 +514,7 @@ __device__ int walk(int3 S, const uint8_t *__restrict__ valid, int64_t cx, int64
         }
         if (leave < 0) return 0;   // cannot happen for a point inside the circumsphere
         T[leave] = e;
-        if (orient(T[0], T[1], T[2], T[3]) < 0) { const LPt s = T[0]; T[0] = T[1]; T[1] = s; }
+        positive_orientation(T);
     }
     return 0;
 }
@@ -409,14 +532,14 @@ __device__ __forceinline__ int64_t orient2(const LPt2 &a, const LPt2 &b, const L
     return (b.u - a.u) * (c.v - a.v) - (b.v - a.v) * (c.u - a.u);
 }
 
-__device__ int perturbed_sign2(const LPt2 (&t)[3], const LPt2 &e);
+__device__ __noinline__ int perturbed_sign2(const LPt2 (&t)[3], const LPt2 &e);
 
 // Sign of the 4 x 4 determinant with rows (u, v, w, 1) of t0, t1, t2, e under
 // the perturbed lifting w = u^2 + v^2 + d_rank: positive when e is inside the
 // circumcircle of the counter-clockwise triangle (t0, t1, t2). Translated so
 // that e is the origin, the unperturbed part is the 3 x 3 determinant of the
 // rows (p - e, |p - e|^2).
-__device__ int lifted_sign2(const LPt2 (&t)[3], const LPt2 &e) {
+__device__ __noinline__ int lifted_sign2(const LPt2 (&t)[3], const LPt2 &e) {
     int64_t r[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -453,7 +576,7 @@ __device__ __noinline__ int perturbed_sign2(const LPt2 (&t)[3], const LPt2 &e) {
 }
 
 // Circumcircle of T (centre and squared radius, FP64), for the filter.
-__device__ void circumcircle(const LPt2 (&T)[3], double (&ctr)[2], double &r2) {
+__device__ __noinline__ void circumcircle(const LPt2 (&T)[3], double (&ctr)[2], double &r2) {
     const double bx = (double)(T[1].u - T[0].u), by = (double)(T[1].v - T[0].v);
     const double cx = (double)(T[2].u - T[0].u), cy = (double)(T[2].v - T[0].v);
     const double d = 2.0 * (bx * cy - by * cx);
@@ -498,46 +621,60 @@ __device__ bool circle_fits(const double (&ctr)[2], double r2, int3 S, const int
 // triangle's circle holds no valid window point and fits in the window, or
 // when no valid point of the face lies strictly on the far side of F (F is
 // then on the hull of the face's points).
-__device__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b,
+__device__ __noinline__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b,
                             int64_t u0, int64_t u1, int64_t v0, int64_t v1, LPt2 (&T)[3], int kf) {
+    const int lane = threadIdx.x & 31;
     const int64_t ext[3] = {S.x, S.y, S.z};
     const LPt2 A = T[(kf + 1) % 3], B = T[(kf + 2) % 3];
     const int64_t sf = orient2(A, B, T[kf]);
+    const int wu = (int)(u1 - u0 + 1), W = wu * (int)(v1 - v0 + 1);
     bool far_pt = false, have = false;
     LPt2 D = A;
-    for (int64_t vv = v0; vv <= v1; ++vv)
-        for (int64_t uu = u0; uu <= u1; ++uu) {
-            int64_t pc[3] = {c[0], c[1], c[2]};
-            pc[a] = uu;
-            pc[b] = vv;
-            const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
-            if (!valid[r] || r == A.rank || r == B.rank) continue;
-            const LPt2 p = {uu - c[a], vv - c[b], r};
-            const int64_t so = orient2(A, B, p);
-            if (so == 0) continue;
-            if ((so > 0) == (sf > 0)) { far_pt = true; continue; }
-            if (!have) { D = p; have = true; continue; }
-            LPt2 t3[3] = {A, B, D};
-            if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
-            if (lifted_sign2(t3, p) > 0) D = p;
-        }
+    for (WinIter w(wu, 1 << 30, lane); w.k < W; w.step()) {
+        int64_t pc[3] = {c[0], c[1], c[2]};
+        pc[a] = u0 + w.x;
+        pc[b] = v0 + w.y;
+        const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+        if (!valid[r] || r == A.rank || r == B.rank) continue;
+        const LPt2 p = {pc[a] - c[a], pc[b] - c[b], r};
+        const int64_t so = orient2(A, B, p);
+        if (so == 0) continue;
+        if ((so > 0) == (sf > 0)) { far_pt = true; continue; }
+        if (!have) { D = p; have = true; continue; }
+        LPt2 t3[3] = {A, B, D};
+        if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
+        if (lifted_sign2(t3, p) > 0) D = p;
+    }
+    far_pt = __any_sync(kAll, far_pt);
+    for (int off = 16; off > 0; off >>= 1) {
+        LPt2 Do;
+        Do.u = __shfl_xor_sync(kAll, (long long)D.u, off);
+        Do.v = __shfl_xor_sync(kAll, (long long)D.v, off);
+        Do.rank = __shfl_xor_sync(kAll, (long long)D.rank, off);
+        const bool ho = __shfl_xor_sync(kAll, (int)have, off) != 0;
+        if (!ho || Do.rank == D.rank) continue;
+        if (!have) { D = Do; have = true; continue; }
+        LPt2 t3[3] = {A, B, D};
+        if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
+        if (lifted_sign2(t3, Do) > 0) D = Do;
+    }
     if (have) {
         LPt2 t3[3] = {A, B, D};
         if (orient2(t3[0], t3[1], t3[2]) < 0) { const LPt2 sw = t3[0]; t3[0] = t3[1]; t3[1] = sw; }
-        bool empty = true;
-        for (int64_t vv = v0; vv <= v1 && empty; ++vv)
-            for (int64_t uu = u0; uu <= u1 && empty; ++uu) {
-                int64_t pc[3] = {c[0], c[1], c[2]};
-                pc[a] = uu;
-                pc[b] = vv;
-                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
-                if (!valid[r] || r == A.rank || r == B.rank || r == D.rank) continue;
-                const LPt2 p = {uu - c[a], vv - c[b], r};
-                if (lifted_sign2(t3, p) > 0) empty = false;
-            }
+        bool inside = false;
+        for (WinIter w(wu, 1 << 30, lane); w.k < W && !inside; w.step()) {
+            int64_t pc[3] = {c[0], c[1], c[2]};
+            pc[a] = u0 + w.x;
+            pc[b] = v0 + w.y;
+            const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+            if (!valid[r] || r == A.rank || r == B.rank || r == D.rank) continue;
+            const LPt2 p = {pc[a] - c[a], pc[b] - c[b], r};
+            inside = lifted_sign2(t3, p) > 0;
+        }
+        inside = __any_sync(kAll, inside);
         double ctr[2], r2;
         circumcircle(t3, ctr, r2);
-        if (empty && circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1)) {
+        if (!inside && circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1)) {
             T[kf] = D;
             return true;
         }
@@ -550,19 +687,21 @@ __device__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int
         const int64_t d = orient2(A, B, o0);
         const int64_t nu = orient2(A, B, eu) - d, nv = orient2(A, B, ev) - d;
         const int64_t sg = sf > 0 ? 1 : -1;
+        const int64_t budget = kHullScanWork / 32;
         int64_t work = 0;
-        for (int64_t vv = 0; vv < ext[b]; ++vv) {
-            if (++work > kHullScanWork) return false;
+        bool stop = false;
+        for (int64_t vv = lane; vv < ext[b] && !stop; vv += 32) {
+            if (++work > budget) { stop = true; break; }
             int64_t t0, t1;
             if (!positive_range(sg * nu, sg * (nv * (vv - c[b]) + d), -c[a], ext[a] - 1 - c[a], t0, t1)) continue;
             for (int64_t t = t0; t <= t1; ++t) {
-                if (++work > kHullScanWork) return false;
                 int64_t pc[3] = {c[0], c[1], c[2]};
                 pc[a] = t + c[a];
                 pc[b] = vv;
-                if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) return false;
+                if (++work > budget || valid[lattice_rank(S, pc[0], pc[1], pc[2])]) { stop = true; break; }
             }
         }
+        if (__any_sync(kAll, stop)) return false;
         T[kf] = A;
         return true;
     }
@@ -570,37 +709,53 @@ __device__ bool across_edge(int3 S, const uint8_t *__restrict__ valid, const int
 }
 
 // The walk of `walk` on the face through c whose free axes are a < b: the
-// window is the square of radius R around c on that face. Points are
-// visited in rank order (axis b outer, axis a inner). Returns 1 with the
-// triangle and q's barycentric coordinates, or 0.
-__device__ int walk2(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b, int R,
+// window is the square of radius R around c on that face, its points in
+// rank order (axis a fastest). Returns 1 with the triangle and q's
+// barycentric coordinates, or 0.
+__device__ __noinline__ int walk2(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a, int b, int R,
                      LPt2 (&T)[3], double (&lam)[3]) {
+    const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t)S.x * S.y * S.z;
     const int64_t ext[3] = {S.x, S.y, S.z};
     const LPt2 q0 = {0, 0, -1};
     const int64_t u0 = max(c[a] - R, (int64_t)0), u1 = min(c[a] + R, ext[a] - 1);
     const int64_t v0 = max(c[b] - R, (int64_t)0), v1 = min(c[b] + R, ext[b] - 1);
+    const int wu = (int)(u1 - u0 + 1), W = wu * (int)(v1 - v0 + 1);
     for (int it = 0; it < kMaxPivots; ++it) {
         double ctr[2], r2;
         circumcircle(T, ctr, r2);
-        const double tol = 1e-9 * (r2 + 1.0);
-        LPt2 e;
-        bool found = false;
-        for (int64_t vv = v0; vv <= v1 && !found; ++vv)
-            for (int64_t uu = u0; uu <= u1 && !found; ++uu) {
-                int64_t pc[3] = {c[0], c[1], c[2]};
-                pc[a] = uu;
-                pc[b] = vv;
-                const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
-                if (!valid[r]) continue;
-                const double du = (double)(uu - c[a]) - ctr[0], dv = (double)(vv - c[b]) - ctr[1];
-                if (du * du + dv * dv > r2 + tol) continue;
-                if (T[0].rank == r || T[1].rank == r || T[2].rank == r) continue;
-                const LPt2 cand = {uu - c[a], vv - c[b], r};
-                if (lifted_sign2(T, cand) > 0) { e = cand; found = true; }
+        const float fc0 = (float)ctr[0], fc1 = (float)ctr[1];
+        const float fr2 = (float)r2 * (1.0f + 1e-4f) + 1e-2f;   // as in walk
+        const bool deep = it < kDeepPivots;   // the pivot rule of walk
+        int64_t best = kNone;
+        unsigned long long bkey = 0;
+        for (WinIter w(wu, 1 << 30, lane); w.k < W; w.step()) {
+            int64_t pc[3] = {c[0], c[1], c[2]};
+            pc[a] = u0 + w.x;
+            pc[b] = v0 + w.y;
+            const int64_t r = lattice_rank(S, pc[0], pc[1], pc[2]);
+            if (!valid[r]) continue;
+            const float du = (float)(pc[a] - c[a]) - fc0, dv = (float)(pc[b] - c[b]) - fc1;
+            const float d2 = du * du + dv * dv;
+            if (d2 > fr2) continue;
+            if (T[0].rank == r || T[1].rank == r || T[2].rank == r) continue;
+            const LPt2 cand = {pc[a] - c[a], pc[b] - c[b], r};
+            if (deep) {
+                const unsigned long long key = depth_key((float)r2 - d2, r);
+                if (key > bkey && lifted_sign2(T, cand) > 0) bkey = key;
+            } else if (lifted_sign2(T, cand) > 0) {
+                best = r;
+                break;
             }
+        }
+        if (deep) {
+            bkey = warp_max_u64(bkey);
+            best = bkey ? (int64_t)(0xffffffffu - (unsigned)(bkey & 0xffffffffu)) : kNone;
+        } else {
+            best = warp_min(best);
+        }
         const int64_t o = orient2(T[0], T[1], T[2]);   // > 0: T is kept counter-clockwise
-        if (!found) {
+        if (best == kNone) {
             int64_t ol[3];
             int nfar = 0, kf = -1;
 #pragma unroll
@@ -615,6 +770,9 @@ __device__ int walk2(int3 S, const uint8_t *__restrict__ valid, const int64_t (&
             if (nfar > 1 || ol[kf] != 0) return 0;
             return across_edge(S, valid, c, a, b, u0, u1, v0, v1, T, kf) ? 1 : 0;
         }
+        int64_t bc[3];
+        rank_coords(S, best, bc);
+        const LPt2 e = {bc[a] - c[a], bc[b] - c[b], best};
         int leave = -1;
         int64_t bq = 0, be = 0;
 #pragma unroll
@@ -640,20 +798,23 @@ __device__ int walk2(int3 S, const uint8_t *__restrict__ valid, const int64_t (&
 }
 
 // ---- Edges: nearest valid neighbours along the free axis a --------------
-__device__ int edge_interp(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a,
+__device__ __noinline__ int edge_interp(int3 S, const uint8_t *__restrict__ valid, const int64_t (&c)[3], int a,
                            int64_t (&vtx)[4], double (&lam)[4]) {
+    const int lane = threadIdx.x & 31;
     const int64_t ext[3] = {S.x, S.y, S.z};
     int64_t pc[3] = {c[0], c[1], c[2]};
-    int64_t lo = -1, hi = -1;
-    for (int64_t t = c[a] - 1; t >= 0 && lo < 0; --t) {
+    int64_t lo = -1, hi = kNone;
+    for (int64_t t = c[a] - 1 - lane; t >= 0; t -= 32) {
         pc[a] = t;
-        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) lo = t;
+        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) { lo = t; break; }
     }
-    for (int64_t t = c[a] + 1; t < ext[a] && hi < 0; ++t) {
+    for (int64_t t = c[a] + 1 + lane; t < ext[a]; t += 32) {
         pc[a] = t;
-        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) hi = t;
+        if (valid[lattice_rank(S, pc[0], pc[1], pc[2])]) { hi = t; break; }
     }
-    if (lo < 0 || hi < 0) return 0;
+    lo = warp_max(lo);
+    hi = warp_min(hi);
+    if (lo < 0 || hi == kNone) return 0;
     pc[a] = lo;
     vtx[0] = lattice_rank(S, pc[0], pc[1], pc[2]);
     pc[a] = hi;
@@ -663,66 +824,94 @@ __device__ int edge_interp(int3 S, const uint8_t *__restrict__ valid, const int6
     return 1;
 }
 
-// One thread per lattice point: valid entries are copied (status 1),
-// missing ones take the barycentric interpolant over their Delaunay
-// tetrahedron (status 2) or stay missing (NaN, status 0).
-__global__ void fill_delaunay_kernel(int3 S, const float *__restrict__ ends, const uint8_t *__restrict__ valid,
-                                     float *__restrict__ out, uint8_t *__restrict__ status) {
+// The missing entry p, solved by the whole warp: the barycentric
+// interpolant over its Delaunay simplex (status 2), or missing (NaN,
+// status 0); lane 0 writes it.
+__device__ void solve_entry(int3 S, int64_t p, const float *__restrict__ ends, const uint8_t *__restrict__ valid,
+                            float *__restrict__ out, uint8_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t)S.x * S.y * S.z;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        if (valid[p]) {
-            out[3 * p] = ends[3 * p]; out[3 * p + 1] = ends[3 * p + 1]; out[3 * p + 2] = ends[3 * p + 2];
-            if (status) status[p] = 1;
+    int64_t c[3];
+    rank_coords(S, p, c);
+    const int64_t cx = c[0], cy = c[1], cz = c[2];
+    const bool fixed[3] = {cx == 0 || cx == S.x - 1, cy == 0 || cy == S.y - 1, cz == 0 || cz == S.z - 1};
+    const int nfix = (int)fixed[0] + (int)fixed[1] + (int)fixed[2];
+    const bool flat = S.x == 1 || S.y == 1 || S.z == 1;
+    int64_t vtx[4] = {-1, -1, -1, -1};
+    double lam[4] = {0.0, 0.0, 0.0, 0.0};
+    int nv = 0, ok = 0;
+    if (flat || nfix == 3) {
+        ok = 0;                                   // no tetrahedra, or a corner
+    } else if (nfix == 0) {
+        LPt T[4];
+        start_tetrahedron(P, T);
+        for (int R = 2; R <= kMaxWindow && !ok; ++R) ok = walk(S, valid, cx, cy, cz, R, T, lam);
+        for (int k = 0; k < 4; ++k) vtx[k] = T[k].rank;
+        nv = 4;
+    } else if (nfix == 1) {
+        const int a = fixed[0] ? 1 : 0, b = fixed[2] ? 1 : 2;
+        LPt2 T2[3];
+        double l2[3];
+        start_triangle(P, T2);
+        for (int R = 2; R <= kMaxWindow2 && !ok; ++R) ok = walk2(S, valid, c, a, b, R, T2, l2);
+        for (int k = 0; k < 3; ++k) { vtx[k] = T2[k].rank; lam[k] = l2[k]; }
+        nv = 3;
+    } else {
+        const int a = !fixed[0] ? 0 : (!fixed[1] ? 1 : 2);
+        ok = edge_interp(S, valid, c, a, vtx, lam);
+        nv = 2;
+    }
+    if (lane != 0) return;
+    if (ok != 1) {
+        const float nan = __int_as_float(0x7fc00000);
+        out[3 * p] = nan; out[3 * p + 1] = nan; out[3 * p + 2] = nan;
+        if (status) status[p] = 0;
+        return;
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < nv; ++k) {
+        const int64_t v = vtx[k];
+        if (v < 0 || v >= P) {   // never: both walks reject starting points
+            (void)BTO_IN_BOUNDS(false, nullptr);
             continue;
         }
-        const int64_t cx = p % S.x, cy = (p / S.x) % S.y, cz = p / ((int64_t)S.x * S.y);
-        const int64_t c[3] = {cx, cy, cz};
-        const bool fixed[3] = {cx == 0 || cx == S.x - 1, cy == 0 || cy == S.y - 1, cz == 0 || cz == S.z - 1};
-        const int nfix = (int)fixed[0] + (int)fixed[1] + (int)fixed[2];
-        const bool flat = S.x == 1 || S.y == 1 || S.z == 1;
-        int64_t vtx[4] = {-1, -1, -1, -1};
-        double lam[4] = {0.0, 0.0, 0.0, 0.0};
-        int nv = 0, ok = 0;
-        if (flat || nfix == 3) {
-            ok = 0;                                   // no tetrahedra, or a corner
-        } else if (nfix == 0) {
-            LPt T[4];
-            start_tetrahedron(P, T);
-            for (int R = 2; R <= kMaxWindow && !ok; ++R) ok = walk(S, valid, cx, cy, cz, R, T, lam);
-            for (int k = 0; k < 4; ++k) vtx[k] = T[k].rank;
-            nv = 4;
-        } else if (nfix == 1) {
-            const int a = fixed[0] ? 1 : 0, b = fixed[2] ? 1 : 2;
-            LPt2 T2[3];
-            double l2[3];
-            start_triangle(P, T2);
-            for (int R = 2; R <= kMaxWindow2 && !ok; ++R) ok = walk2(S, valid, c, a, b, R, T2, l2);
-            for (int k = 0; k < 3; ++k) { vtx[k] = T2[k].rank; lam[k] = l2[k]; }
-            nv = 3;
-        } else {
-            const int a = !fixed[0] ? 0 : (!fixed[1] ? 1 : 2);
-            ok = edge_interp(S, valid, c, a, vtx, lam);
-            nv = 2;
-        }
-        if (ok != 1) {
-            const float nan = __int_as_float(0x7fc00000);
-            out[3 * p] = nan; out[3 * p + 1] = nan; out[3 * p + 2] = nan;
-            if (status) status[p] = 0;
-            continue;
-        }
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < nv; ++k) {
-            const int64_t v = vtx[k];
-            if (v < 0 || v >= P) {   // never: both walks reject starting points
-                (void)BTO_IN_BOUNDS(false, nullptr);
-                continue;
-            }
 #pragma unroll
-            for (int d = 0; d < 3; ++d) acc[d] += lam[k] * (double)ends[3 * v + d];
+        for (int d = 0; d < 3; ++d) acc[d] += lam[k] * (double)ends[3 * v + d];
+    }
+    out[3 * p] = (float)acc[0]; out[3 * p + 1] = (float)acc[1]; out[3 * p + 2] = (float)acc[2];
+    if (status) status[p] = 2;
+}
+
+constexpr int kFillThreads = 128;
+
+// Each warp takes chunks of 32 lattice points (grid-stride): valid entries
+// are copied (status 1) by their lanes, and the warp then solves the
+// chunk's missing entries one after another, all lanes on each.
+__global__ void __launch_bounds__(kFillThreads) fill_delaunay_kernel(int3 S, const float *__restrict__ ends,
+                                                                     const uint8_t *__restrict__ valid,
+                                                                     float *__restrict__ out,
+                                                                     uint8_t *__restrict__ status) {
+    const int64_t P = (int64_t)S.x * S.y * S.z;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < P; base += nwarps * 32) {
+        const int64_t p = base + lane;
+        bool miss = false;
+        if (p < P) {
+            if (valid[p]) {
+                out[3 * p] = ends[3 * p]; out[3 * p + 1] = ends[3 * p + 1]; out[3 * p + 2] = ends[3 * p + 2];
+                if (status) status[p] = 1;
+            } else {
+                miss = true;
+            }
         }
-        out[3 * p] = (float)acc[0]; out[3 * p + 1] = (float)acc[1]; out[3 * p + 2] = (float)acc[2];
-        if (status) status[p] = 2;
+        unsigned m = __ballot_sync(kAll, miss);
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            solve_entry(S, base + bit, ends, valid, out, status);
+        }
     }
 }
 
@@ -732,7 +921,7 @@ BTO_BOUNDS_ACCESSOR(bounds_failures_delaunay)
 
 cudaError_t launch_fill_delaunay(const int32_t S[3], const float *ends, const uint8_t *valid, float *out,
                                  uint8_t *status, int grid, cudaStream_t s) {
-    fill_delaunay_kernel<<<grid, 128, 0, s>>>(make_int3(S[0], S[1], S[2]), ends, valid, out, status);
+    fill_delaunay_kernel<<<grid, kFillThreads, 0, s>>>(make_int3(S[0], S[1], S[2]), ends, valid, out, status);
     return cudaGetLastError();
 }
 

@@ -151,3 +151,53 @@ def test_entries_on_the_hull_of_the_valid_points(S, k, seed):
     assert np.sum(on_plane & (st_o == 2)) > 10 and np.all(st_o[(t > k) & ~v] == 0)
     filled = st_o == 2
     assert np.max(np.abs(got[filled] - ref[filled])) <= 2e-6 * np.abs(ref[filled]).max()
+
+
+def test_large_lattice_sampled_against_local_oracle():
+    """A 96 x 96 x 64 lattice with the hole pattern of block faces (slabs two
+    points thick at 47-48 along x and along y, 2% random holes, four
+    spherical voids) is filled whole on the GPU. For sampled missing entries
+    at least 6 points from the lattice's faces, the oracle triangulates the
+    13^3 neighbourhood around the entry. Where the tetrahedron holding the
+    entry has a circumsphere that no lattice point outside the neighbourhood
+    can enter, it is also the tetrahedron of the whole lattice, and the GPU
+    must have filled the entry with the same interpolant."""
+    S = (96, 96, 64)
+    P = int(np.prod(S))
+    X = oracle.lattice_coords(S, np.arange(P)).astype(np.int64)
+    rng = np.random.default_rng(31)
+    v = rng.random(P) > 0.02
+    v &= ~np.isin(X[:, 0], (47, 48)) & ~np.isin(X[:, 1], (47, 48))
+    for _ in range(4):
+        c = rng.uniform(10, np.array(S) - 11)
+        v &= np.linalg.norm(X - c, axis=1) > rng.uniform(2.0, 3.0)
+    ends = np.stack([X[:, 0] + 0.3 * np.sin(0.21 * X[:, 1]), X[:, 1] + 0.2 * np.cos(0.17 * X[:, 2] + 0.1 * X[:, 0]),
+                     X[:, 2] + 0.01 * X[:, 0] * X[:, 1] / 9.0], axis=1).astype(np.float32)
+    got, st = _gpu_fill(S, np.where(v[:, None], ends, np.nan).astype(np.float32), v)
+    inner = np.all((X >= 6) & (X <= np.array(S) - 7), axis=1) & ~v
+    sample = rng.choice(np.flatnonzero(inner), size=32, replace=False)
+    S2 = (13, 13, 13)
+    off = oracle.lattice_coords(S2, np.arange(13 ** 3)).astype(np.int64) - 6
+    checked = 0
+    for j in sample:
+        g = X[j] + off
+        gid = g[:, 0] + S[0] * (g[:, 1] + S[1] * g[:, 2])
+        tets = oracle.delaunay(S2, v[gid])
+        V = oracle.lattice_coords(S2, tets)
+        A = np.transpose(V[:, 1:, :] - V[:, :1, :], (0, 2, 1))
+        lam3 = np.einsum("tij,tj->ti", np.linalg.inv(A), np.array([6.0, 6.0, 6.0]) - V[:, 0, :])
+        lam = np.concatenate([1.0 - lam3.sum(axis=1, keepdims=True), lam3], axis=1)
+        hit = np.flatnonzero(np.all(lam >= -1e-9, axis=1))
+        if hit.size == 0:
+            continue
+        t = hit[0]
+        M = 2.0 * (V[t, 1:] - V[t, :1])
+        ctr = np.linalg.solve(M, (V[t, 1:] ** 2).sum(axis=1) - (V[t, 0] ** 2).sum())
+        rad = np.sqrt(((V[t, 0] - ctr) ** 2).sum())
+        if np.any(ctr - rad <= -1.0 + 1e-6) or np.any(ctr + rad >= 13.0 - 1e-6):
+            continue
+        want = lam[t] @ ends[gid[tets[t]]].astype(np.float64)
+        assert st[j] == 2, (X[j], st[j])
+        assert np.max(np.abs(got[j] - want)) <= 2e-6 * np.abs(ends).max(), (X[j], got[j], want)
+        checked += 1
+    assert checked >= 20, checked
