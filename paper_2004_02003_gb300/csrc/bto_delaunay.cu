@@ -196,6 +196,33 @@ __device__ __noinline__ void circumsphere(const LPt (&T)[4], double (&ctr)[3], d
     r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
 }
 
+// The circumsphere of T for the walk's filter: centre and squared radius in
+// FP32, relative to q. The 3 x 3 system 2 (p_m - a) . c = |p_m - a|^2 is
+// solved by Cramer's rule in exact 64-bit integers (differences below 2^12:
+// the determinant stays below 2^42 and the numerators below 2^55); only the
+// conversions, the three quotients and the final sums are rounded, so the
+// centre is within 3e-7 r of the exact one (T holds q, so |c - q| <= r).
+__device__ __forceinline__ void circumsphere_f(const LPt (&T)[4], float (&c)[3], float &r2) {
+    int64_t A[3][3], b[3];
+    const LPt &a = T[0];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const LPt &p = T[m + 1];
+        A[m][0] = 2 * (p.x - a.x);
+        A[m][1] = 2 * (p.y - a.y);
+        A[m][2] = 2 * (p.z - a.z);
+        b[m] = (p.x - a.x) * (p.x - a.x) + (p.y - a.y) * (p.y - a.y) + (p.z - a.z) * (p.z - a.z);
+    }
+    const float det = (float)det3(A[0][0], A[0][1], A[0][2], A[1][0], A[1][1], A[1][2], A[2][0], A[2][1], A[2][2]);
+    const float u0 = (float)det3(b[0], A[0][1], A[0][2], b[1], A[1][1], A[1][2], b[2], A[2][1], A[2][2]) / det;
+    const float u1 = (float)det3(A[0][0], b[0], A[0][2], A[1][0], b[1], A[1][2], A[2][0], b[2], A[2][2]) / det;
+    const float u2 = (float)det3(A[0][0], A[0][1], b[0], A[1][0], A[1][1], b[1], A[2][0], A[2][1], b[2]) / det;
+    c[0] = u0 + (float)a.x;
+    c[1] = u1 + (float)a.y;
+    c[2] = u2 + (float)a.z;
+    r2 = u0 * u0 + u1 * u1 + u2 * u2;
+}
+
 // Sets T to the four far starting points (positively oriented).
 __device__ void start_tetrahedron(int64_t P, LPt (&T)[4]) {
     const int64_t far[4][3] = {{kFar, kFar, kFar}, {kFar, -kFar, -kFar}, {-kFar, kFar, -kFar}, {-kFar, -kFar, kFar}};
@@ -430,16 +457,16 @@ __device__ __noinline__ int walk(int3 S, const uint8_t *__restrict__ valid, int6
         // entering point: the lowest-ranked valid window point inside the
         // circumsphere of T (each lane takes the first of its points in rank
         // order, the warp the least of those). A point clearly outside by
-        // its FP32 distance to the centre is skipped. T holds q, so the
-        // centre lies within r of q, and near the sphere the squared
-        // distance's rounding error stays below 1e-6 r^2: with the margin
-        // 1e-4 r^2 + 1e-2 only points strictly outside are skipped; every
-        // other point gets the exact predicate, so the choice is the exact
-        // one.
-        double ctr[3], r2;
-        circumsphere(T, ctr, r2);
-        const float fc0 = (float)ctr[0], fc1 = (float)ctr[1], fc2 = (float)ctr[2];
-        const float fr2 = (float)r2 * (1.0f + 1e-4f) + 1e-2f;
+        // its FP32 distance to the centre (circumsphere_f) is skipped. T
+        // holds q, so the centre lies within r of q, and near the sphere the
+        // squared distance's rounding error stays below 2e-6 r^2: with the
+        // margin 1e-4 r^2 + 1e-2 only points strictly outside are skipped;
+        // every other point gets the exact predicate, so the choice is the
+        // exact one.
+        float fc[3], fr2e;
+        circumsphere_f(T, fc, fr2e);
+        const float fc0 = fc[0], fc1 = fc[1], fc2 = fc[2];
+        const float fr2 = fr2e * (1.0f + 1e-4f) + 1e-2f;
         const bool deep = it < kDeepPivots;
         int64_t best = kNone;
         unsigned long long bkey = 0;
@@ -453,7 +480,7 @@ __device__ __noinline__ int walk(int3 S, const uint8_t *__restrict__ valid, int6
             if (T[0].rank == r || T[1].rank == r || T[2].rank == r || T[3].rank == r) continue;
             const LPt p = {x - cx, y - cy, z - cz, r};
             if (deep) {
-                const unsigned long long key = depth_key((float)r2 - d2, r);
+                const unsigned long long key = depth_key(fr2e - d2, r);
                 if (key > bkey && lifted_sign(T, p) < 0) bkey = key;
             } else if (lifted_sign(T, p) < 0) {
                 best = r;
@@ -479,9 +506,13 @@ __device__ __noinline__ int walk(int3 S, const uint8_t *__restrict__ valid, int6
                 lam[k] = (double)ol[k] / (double)o;
                 if (T[k].rank >= P) { ++nfar; kf = k; }
             }
-            // the circumsphere must fit in the window: then no lattice
-            // point outside the window is inside it
-            if (nfar == 0) return sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1) ? 1 : 0;
+            // the circumsphere (FP64) must fit in the window: then no
+            // lattice point outside the window is inside it
+            if (nfar == 0) {
+                double ctr[3], r2;
+                circumsphere(T, ctr, r2);
+                return sphere_fits(ctr, r2, S, cx, cy, cz, x0, x1, y0, y1, z0, z1) ? 1 : 0;
+            }
             // a starting point with weight above 0: q is outside the hull
             // of the window's valid points; with weight 0: q is on a facet
             if (nfar > 1 || ol[kf] != 0) return 0;
@@ -584,6 +615,18 @@ __device__ __noinline__ void circumcircle(const LPt2 (&T)[3], double (&ctr)[2], 
     const double ux = (cy * b2 - by * c2) / d, uy = (bx * c2 - cx * b2) / d;
     ctr[0] = ux + (double)T[0].u;
     ctr[1] = uy + (double)T[0].v;
+    r2 = ux * ux + uy * uy;
+}
+
+// The circumcircle of T for the face walk's filter, as circumsphere_f:
+// exact 64-bit Cramer numerators, FP32 quotients.
+__device__ __forceinline__ void circumcircle_f(const LPt2 (&T)[3], float (&c)[2], float &r2) {
+    const int64_t bx = T[1].u - T[0].u, by = T[1].v - T[0].v, cx = T[2].u - T[0].u, cy = T[2].v - T[0].v;
+    const int64_t b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    const float d = (float)(2 * (bx * cy - by * cx));
+    const float ux = (float)(cy * b2 - by * c2) / d, uy = (float)(bx * c2 - cx * b2) / d;
+    c[0] = ux + (float)T[0].u;
+    c[1] = uy + (float)T[0].v;
     r2 = ux * ux + uy * uy;
 }
 
@@ -722,10 +765,10 @@ __device__ __noinline__ int walk2(int3 S, const uint8_t *__restrict__ valid, con
     const int64_t v0 = max(c[b] - R, (int64_t)0), v1 = min(c[b] + R, ext[b] - 1);
     const int wu = (int)(u1 - u0 + 1), W = wu * (int)(v1 - v0 + 1);
     for (int it = 0; it < kMaxPivots; ++it) {
-        double ctr[2], r2;
-        circumcircle(T, ctr, r2);
-        const float fc0 = (float)ctr[0], fc1 = (float)ctr[1];
-        const float fr2 = (float)r2 * (1.0f + 1e-4f) + 1e-2f;   // as in walk
+        float fc[2], fr2e;
+        circumcircle_f(T, fc, fr2e);
+        const float fc0 = fc[0], fc1 = fc[1];
+        const float fr2 = fr2e * (1.0f + 1e-4f) + 1e-2f;   // as in walk
         const bool deep = it < kDeepPivots;   // the pivot rule of walk
         int64_t best = kNone;
         unsigned long long bkey = 0;
@@ -741,7 +784,7 @@ __device__ __noinline__ int walk2(int3 S, const uint8_t *__restrict__ valid, con
             if (T[0].rank == r || T[1].rank == r || T[2].rank == r) continue;
             const LPt2 cand = {pc[a] - c[a], pc[b] - c[b], r};
             if (deep) {
-                const unsigned long long key = depth_key((float)r2 - d2, r);
+                const unsigned long long key = depth_key(fr2e - d2, r);
                 if (key > bkey && lifted_sign2(T, cand) > 0) bkey = key;
             } else if (lifted_sign2(T, cand) > 0) {
                 best = r;
@@ -766,7 +809,11 @@ __device__ __noinline__ int walk2(int3 S, const uint8_t *__restrict__ valid, con
                 lam[k] = (double)ol[k] / (double)o;
                 if (T[k].rank >= P) { ++nfar; kf = k; }
             }
-            if (nfar == 0) return circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1) ? 1 : 0;
+            if (nfar == 0) {
+                double ctr[2], r2;
+                circumcircle(T, ctr, r2);
+                return circle_fits(ctr, r2, S, c, a, b, u0, u1, v0, v1) ? 1 : 0;
+            }
             if (nfar > 1 || ol[kf] != 0) return 0;
             return across_edge(S, valid, c, a, b, u0, u1, v0, v1, T, kf) ? 1 : 0;
         }
