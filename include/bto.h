@@ -306,7 +306,7 @@ BTO_API bto_status bto_fill_lattice(const int32_t lattice[3], const float *d_end
  * Delaunay tetrahedron of the valid lattice points that holds its own
  * lattice point. Ties among cospherical lattice points are broken by
  * infinitesimal lifted weights ordered by canonical lattice id. Each
- * missing entry is solved over the valid points within 2 to 6 lattice
+ * missing entry is solved over the valid points within 2 to 8 lattice
  * units of it, 2 to 12 on a boundary face (the smallest window that
  * holds its simplex's circumsphere). An entry on a boundary face of the
  * lattice lies on the hull of the valid points and takes the interpolant

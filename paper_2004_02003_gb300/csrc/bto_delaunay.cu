@@ -20,7 +20,7 @@
 // circumsphere. The result is the Delaunay tetrahedron of all valid points
 // when its circumsphere fits in the window (no lattice point outside the
 // window can then lie inside it); otherwise the window grows (radius 2 to
-// 6 lattice units) and the walk resumes.
+// 8 lattice units) and the walk resumes.
 //
 // Entries on the lattice's outer faces lie on the hull of the valid points.
 // There the face's plane supports the lifted point set, so the tetrahedra
@@ -136,7 +136,7 @@ __device__ __forceinline__ int64_t lattice_rank(int3 S, int64_t x, int64_t y, in
 
 constexpr int64_t kFar = 1024;   // distance of the four starting points, lattice units
 constexpr int kMaxPivots = 512;
-constexpr int kMaxWindow = 6;      // largest window radius, lattice units
+constexpr int kMaxWindow = 8;      // largest window radius, lattice units
 constexpr int kMaxWindow2 = 12;    // on a face (a window of 25 x 25 points)
 // Work limit (rows plus points) of the scan that shows that a facet (edge)
 // through the query point bounds the hull of all valid points.
@@ -285,7 +285,7 @@ __device__ __forceinline__ void positive_orientation(LPt (&t)[4]) {
 
 // A lane's walk over a window of wx x wy x wz points in rank order: points
 // k = lane, lane + 32, ..., with offsets (x, y, z) inside the window kept
-// by additions (a window holds at most 25 x 25 or 13 x 13 x 13 points, and
+// by additions (a window holds at most 25 x 25 or 17 x 17 x 17 points, and
 // a lattice at most 2^31, so 32-bit indices suffice).
 struct WinIter {
     int wx, wy, k, x, y, z;
