@@ -1281,8 +1281,24 @@ def e2e(args, ctx, fields, dt, dev, stream, nb, world=1):
     el = time.perf_counter() - t
     # whole job: all ranks' units over the slowest rank's time
     _, _, value = aggregate(units, el, world)
+    # this machine's host link: the same per-cycle copies alone, one interval's
+    # worth back to back on the copy stream (no kernels), and the end-to-end
+    # rate those copies would allow
+    cs = copy_streams[0]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(cs)
+    with torch.cuda.stream(cs):
+        for c in range(L):
+            slots[c & 1].copy_(host[c % R], non_blocking=True)
+    c1.record(cs)
+    torch.cuda.synchronize()
+    link_gbs = h2d_bytes * L / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    per_interval = units / max(1, args.steps)
     return {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d_bytes * L,
-            "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R, "copy_streams": K}
+            "d2h_bytes_per_step": d2h_bytes, "host_field_ring": R, "copy_streams": K,
+            "h2d_gbs_copies_alone": link_gbs,
+            "ceiling_value_from_copies_alone": per_interval * world / (h2d_bytes * L / (link_gbs * 1e9))}
 
 
 # ---------------------------------------------------------------------------
