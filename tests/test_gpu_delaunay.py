@@ -201,3 +201,63 @@ def test_large_lattice_sampled_against_local_oracle():
         assert np.max(np.abs(got[j] - want)) <= 2e-6 * np.abs(ends).max(), (X[j], got[j], want)
         checked += 1
     assert checked >= 20, checked
+
+
+def test_large_lattice_face_entries_against_local_oracle():
+    """Face entries of the same kind of lattice: for sampled missing entries
+    on the faces x = 0 and z = S_z - 1 (6 or more points from the face's
+    edges), the oracle triangulates the 13 x 13 x 7 neighbourhood that the
+    face bounds. The tetrahedron holding the entry meets the face in a
+    triangle of the face's own triangulation; where that triangle's
+    circumcircle stays inside the neighbourhood's extent on the face, it is
+    the triangle of the whole lattice, and the GPU's value must equal the
+    oracle's."""
+    S = (64, 72, 48)
+    P = int(np.prod(S))
+    X = oracle.lattice_coords(S, np.arange(P)).astype(np.int64)
+    rng = np.random.default_rng(37)
+    face = (X[:, 0] == 0) | (X[:, 2] == S[2] - 1)
+    v = ~(face & (rng.random(P) < 0.3)) & (rng.random(P) > 0.02)
+    ends = np.stack([X[:, 0] + 0.2 * np.sin(0.3 * X[:, 1]), X[:, 1] + 0.1 * X[:, 2] / 7.0,
+                     X[:, 2] + 0.25 * np.cos(0.2 * X[:, 0] + 0.1 * X[:, 1])], axis=1).astype(np.float32)
+    got, st = _gpu_fill(S, np.where(v[:, None], ends, np.nan).astype(np.float32), v)
+    checked = 0
+    for fixed_axis, at in ((0, 0), (2, S[2] - 1)):
+        free = [a for a in range(3) if a != fixed_axis]
+        cand = (X[:, fixed_axis] == at) & ~v
+        for a in free:
+            cand &= (X[:, a] >= 6) & (X[:, a] <= S[a] - 7)
+        for j in rng.choice(np.flatnonzero(cand), size=12, replace=False):
+            S2 = [13, 13, 13]
+            S2[fixed_axis] = 7
+            lo = X[j].copy()
+            for a in free:
+                lo[a] -= 6
+            lo[fixed_axis] = 0 if at == 0 else at - 6
+            loc = oracle.lattice_coords(S2, np.arange(int(np.prod(S2)))).astype(np.int64)
+            g = loc + lo
+            gid = g[:, 0] + S[0] * (g[:, 1] + S[1] * g[:, 2])
+            q = (X[j] - lo).astype(np.float64)
+            tets = oracle.delaunay(S2, v[gid])
+            V = oracle.lattice_coords(S2, tets)
+            A = np.transpose(V[:, 1:, :] - V[:, :1, :], (0, 2, 1))
+            lam3 = np.einsum("tij,tj->ti", np.linalg.inv(A), q - V[:, 0, :])
+            lam = np.concatenate([1.0 - lam3.sum(axis=1, keepdims=True), lam3], axis=1)
+            hit = np.flatnonzero(np.all(lam >= -1e-9, axis=1))
+            if hit.size == 0:
+                continue
+            t = hit[0]
+            on = np.flatnonzero(V[t, :, fixed_axis] == q[fixed_axis])
+            if on.size != 3:
+                continue
+            W = V[t][on][:, free]
+            M = 2.0 * (W[1:] - W[:1])
+            ctr = np.linalg.solve(M, (W[1:] ** 2).sum(axis=1) - (W[0] ** 2).sum())
+            rad = np.sqrt(((W[0] - ctr) ** 2).sum())
+            if np.any(ctr - rad <= -1.0 + 1e-6) or np.any(ctr + rad >= 13.0 - 1e-6):
+                continue
+            want = lam[t] @ ends[gid[tets[t]]].astype(np.float64)
+            assert st[j] == 2, (X[j], st[j])
+            assert np.max(np.abs(got[j] - want)) <= 2e-6 * np.abs(ends).max(), (X[j], got[j], want)
+            checked += 1
+    assert checked >= 12, checked
