@@ -70,7 +70,7 @@ typedef enum {
     BTO_ERR_CUDA = 3,        /* a CUDA call or launch failed */
     BTO_ERR_OOM = 4,         /* device or host allocation failed */
     BTO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    BTO_ERR_UNSUPPORTED = 6, /* valid request the library does not handle (a fixed capacity exceeded) */
+    BTO_ERR_UNSUPPORTED = 6, /* valid request in a configuration the library does not support */
     BTO_ERR_BOUNDS = 7       /* a bounds check failed (bounds-checked builds only) */
 } bto_status;
 
